@@ -1,0 +1,225 @@
+/*
+ * gpsoc.h -- C ABI of the GB300 ground-state solver for rotating
+ * spin-orbit-coupled spin-1 Bose-Einstein condensates (arXiv 2602.17950).
+ *
+ * The library minimises the discretised energy functional (Section 1, Eq. energy)
+ * on the unit sphere (Eqs. groundstate, sphere) with the preconditioned nonlinear
+ * conjugate gradient method (Section 3.1, Algorithms 1 and 2), the combined
+ * preconditioner (Section 3.4, Eq. PreCondMix) and cascadic multigrid
+ * (Section 3.3, Algorithm 3), on a periodic Fourier-spectral grid
+ * (Section 3.2).  All numerical work runs in CUDA kernels on the current device.
+ *
+ * Conventions shared by every entry point
+ *   - Wave function layout: [solve][component][z][y][x], x fastest, components
+ *     ordered (phi_1, phi_0, phi_-1), each value a complex number stored as two
+ *     doubles (re, im).  One solve holds 3 * nx * ny (* nz) complex values.
+ *   - Grid (Section 3.2): box prod_i [-L_i, L_i], n_i even points per axis,
+ *     h_i = 2 L_i / n_i, x_m = -L_i + m h_i.  The GPU FFTs need every n_i to be
+ *     a power of two in [8, 1024].
+ *   - Integrals are h^d times sums over grid points; <v,u> = h^d sum v conj(u).
+ *   - Host pointers are owned by the caller and only read or written during the
+ *     call.  Device pointers passed in are borrowed for the call only and must
+ *     be valid on the problem's CUDA stream.
+ *   - Every call returns a gpsoc_status; none throws.  On failure
+ *     gpsoc_last_error() gives a message (thread-local, valid until the next
+ *     call on that thread).
+ *   - The library allocates and owns all device memory of a problem; it is
+ *     released by gpsoc_destroy.
+ */
+#ifndef GPSOC_H
+#define GPSOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPSOC_OK = 0,
+  GPSOC_EINVAL = 1,      /* invalid argument (sizes, NULL pointers, options) */
+  GPSOC_ENOMEM = 2,      /* device or host allocation failed */
+  GPSOC_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  GPSOC_ENOTCONV = 4,    /* max_iter reached before the stopping criterion */
+  GPSOC_ENONFINITE = 5,  /* a reduction (energy, mu, norms) became NaN or Inf */
+  GPSOC_ETIMEOUT = 6,    /* a bounded host wait ran out */
+  GPSOC_ESTATE = 7,      /* call made in the wrong state (e.g. solve before set_initial) */
+  GPSOC_EBUDGET = 8,     /* the request does not fit the memory budget */
+  GPSOC_ESTAGNATED = 9   /* Algorithm 2 found no energy decrease (converged to rounding) */
+} gpsoc_status;
+
+enum { GPSOC_TRAP_HARMONIC = 0, GPSOC_TRAP_HARMONIC_QUARTIC = 1, GPSOC_TRAP_USER = 2 };
+enum { GPSOC_FP64 = 0, GPSOC_MIXED = 1 };
+enum { GPSOC_STOP_DPHI = 1, GPSOC_STOP_RES = 2, GPSOC_STOP_ENERGY = 3 };
+
+/* Grid of Section 3.2.  dim = 2 or 3; n[i], L[i] for x, y(, z). */
+typedef struct {
+  int dim;
+  int n[3];
+  double L[3];
+} gpsoc_grid;
+
+/* Trapping potential V(x) (Eq. harmonic, Eq. harm-quart):
+ *   V = 1/2 sum_i g[i]^2 x_i^2 + quad * r^2 + quart * r^4 (+ user_V),
+ * r^2 summed over all dim axes.  HARMONIC uses g only; HARMONIC_QUARTIC adds
+ * quad and quart; USER adds user_V (host array of nx*ny*nz doubles, [z][y][x],
+ * copied at create; only allowed with single-level solves). */
+typedef struct {
+  int kind;
+  double g[3];
+  double quad, quart;
+  const double* user_V;
+} gpsoc_trap;
+
+/* Physical parameters of one solve: rotation speed Omega, SOC strength gamma,
+ * spin-independent interaction beta0 (= c0) and spin-exchange interaction
+ * beta1 (= c1) (Section 1, after Eq. GPE3). */
+typedef struct {
+  double Omega, gamma, beta0, beta1;
+} gpsoc_params;
+
+/* Solver options.
+ *   precision    GPSOC_FP64 or GPSOC_MIXED (FP32 transforms and pointwise work
+ *                with FP64 reductions, then FP64 polishing to tol).
+ *   stop         stopping criterion (Section 3.4, Eqs. stop1-stop3).
+ *   tol          tolerance of that criterion.
+ *   res_tol      if > 0, additionally require max_l ||r_l||_inf < res_tol.
+ *   max_iter     iteration cap per multigrid level.
+ *   theta_trial, sigma, max_halvings: Algorithm 2 (trial step, backtracking
+ *                factor, cap on halvings).  Zero selects 0.1, 0.5, 40.
+ *   cm_levels    1 = plain PCG on the grid; k > 1 = Algorithm 3 starting on the
+ *                grid coarsened by 2^(k-1) per axis (the initial guess must then
+ *                be given on that coarsest grid).
+ *   check_every  iterations run between host convergence checks (0 = 16). */
+typedef struct {
+  int precision;
+  int stop;
+  double tol;
+  double res_tol;
+  int max_iter;
+  double theta_trial, sigma;
+  int max_halvings;
+  int cm_levels;
+  int check_every;
+} gpsoc_opts;
+
+/* Per-solve result.  energy, mu, mass[] describe the final iterate;
+ * res_inf = max_l ||r_l||_inf of that iterate; dE_last = energy change of the
+ * last accepted step. */
+typedef struct {
+  int status;            /* gpsoc_status of this solve */
+  int iters;             /* iterations on the finest level */
+  int total_iters;       /* iterations summed over levels */
+  int levels;
+  int beta_resets, halvings, fp32_iters, fp64_iters;
+  double energy, mu, mass[3], res_inf, dE_last;
+} gpsoc_result;
+
+typedef struct gpsoc_problem gpsoc_problem;
+
+/* Create a problem of `batch` independent solves that share grid and trap and
+ * differ in physical parameters params[0..batch-1].  cuda_stream is a
+ * cudaStream_t (NULL = the library creates its own).  The grid given is the
+ * finest one.  Returns EINVAL for odd or non-power-of-two sizes, L <= 0,
+ * batch < 1, non-finite parameters; ENOMEM if device memory runs out. */
+gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap,
+                          const gpsoc_params* params, int batch, void* cuda_stream,
+                          gpsoc_problem** out);
+
+/* Destroy a problem and free its device memory.  NULL is ignored. */
+void gpsoc_destroy(gpsoc_problem* p);
+
+/* Size in complex values of one solve's wave function on the grid of level
+ * `level` (0 = finest, 1 = finest/2 per axis, ...). */
+size_t gpsoc_solve_size(const gpsoc_problem* p, int level);
+
+/* Set the initial guess of every solve from host memory (batch * 3 * npts
+ * complex as interleaved doubles) on the grid of `level` (0 = finest; use
+ * cm_levels - 1 for a multigrid solve).  Each solve is normalised to total
+ * mass 1 (Eq. mass), keeping its component mass ratios. */
+gpsoc_status gpsoc_set_initial(gpsoc_problem* p, const double* psi, int level);
+
+/* Same from device memory (complex128, or complex64 if is_fp32). */
+gpsoc_status gpsoc_set_initial_device(gpsoc_problem* p, const void* dptr, int is_fp32, int level);
+
+/* Initial guesses (a)-(f) of Section 4: kind[c] in 0..9 = a, b, b_bar, c,
+ * c_bar, d, d_bar, e, e_bar, f for component c, divided by sqrt(3) and
+ * normalised; generated on the device for every solve on the grid of `level`.
+ * Guess (f) requires beta0 > 0 and a harmonic trap. */
+gpsoc_status gpsoc_set_initial_kind(gpsoc_problem* p, const int kind[3], int level);
+
+/* Run Algorithm 3 (or Algorithm 1 if opts->cm_levels == 1) for every solve to
+ * the stopping criterion.  results (may be NULL) receives batch entries.  The
+ * call returns GPSOC_OK when every solve converged, else the first failing
+ * solve's status; per-solve status is in results[]. */
+gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result* results);
+
+/* Run exactly `iters` PCG iterations on the current level and state without
+ * any stopping test (restart = 1 starts with beta = 0).  For step-by-step
+ * comparison with a reference implementation. */
+gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int restart,
+                           gpsoc_result* results);
+
+/* Copy the current wave functions to host memory (batch * 3 * npts complex). */
+gpsoc_status gpsoc_get_psi(const gpsoc_problem* p, double* psi_out);
+
+/* Copy the current wave functions to device memory (complex128). */
+gpsoc_status gpsoc_get_psi_device(const gpsoc_problem* p, void* dptr);
+
+/* Energy (Eq. energy), chemical potential (Eq. muphi) and component masses of
+ * the current iterate of every solve (arrays of length batch, mass 3*batch). */
+gpsoc_status gpsoc_get_observables(gpsoc_problem* p, double* E, double* mu, double* mass);
+
+/* Operator-level entry points (Sections 2.2, 3.1, 3.4) on the current level.
+ * Host arrays as in gpsoc_set_initial.
+ *   gpsoc_apply_h: H_l(Phi) of Eqs. eigen1-eigen3 for the current state into
+ *     hpsi (may be NULL); obs (may be NULL) receives per solve 9 doubles:
+ *     E, mu, alpha_1, alpha_0, alpha_-1 (Eq. PreCnstAlpha), mass_1, mass_0,
+ *     mass_-1, <H_lin Phi, Phi>.
+ *   gpsoc_apply_precond: P_C r (Eq. PreCondMix) for the current state's alpha
+ *     and density, r given per solve; result into out.
+ *   gpsoc_step_model: for directions P (one per solve, tangent or not), the
+ *     coefficients a_n, b_n (Eqs. an, bn; H_l(P) read with the density frozen at
+ *     Phi) and the energy change E(cos t Phi + sin t P/||P||) - E(Phi) at
+ *     n_theta angles theta[]; out receives per solve 2 + n_theta doubles. */
+gpsoc_status gpsoc_apply_h(gpsoc_problem* p, double* hpsi, double* obs);
+gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, const double* r, double* out);
+gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* theta, int n_theta,
+                              double* out);
+
+/* Spectral zero-padding prolongation (Section 3.3, step c; read as zero
+ * padding) of every solve from level `level` to level `level - 1`, followed by
+ * renormalisation to unit mass; the result becomes the current state. */
+gpsoc_status gpsoc_prolong(gpsoc_problem* p, int level);
+
+/* Batched 1-D FFTs along one axis (axis 0 = x, 1 = y, 2 = z) of `count`
+ * arrays laid out like one component on the problem's finest grid, in place on
+ * device memory `data` (complex128).  inverse != 0 applies the inverse
+ * transform including 1/n (Section 3.2 convention, forward unnormalised). */
+gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, int inverse);
+
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ *   gpsoc_profile: run `iters` PCG iterations from the current state (beta
+ *     restarted, no stopping test) with a CUDA event recorded after every
+ *     kernel on the problem's stream; ms[k] receives the average duration of the
+ *     k-th kernel of an iteration (at most cap entries), *n_kernels the number
+ *     of kernels per iteration.  The state advances by `iters` iterations.
+ *   gpsoc_profile_name: name of the k-th kernel of the last profile ("" if none).
+ *   gpsoc_kernel_launches: number of kernels this problem has launched so far
+ *     (each replay of a captured iteration graph counts all its kernels). */
+gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, double* ms, int cap, int* n_kernels);
+const char* gpsoc_profile_name(const gpsoc_problem* p, int k);
+uint64_t gpsoc_kernel_launches(const gpsoc_problem* p);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char* gpsoc_last_error(void);
+
+/* Library version string. */
+const char* gpsoc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPSOC_H */

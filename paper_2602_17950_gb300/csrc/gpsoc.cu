@@ -1,0 +1,948 @@
+// C ABI of libgpsoc: problem object, device memory, the PCG / CM-PCG driver.
+//
+// The driver keeps every solve's state on the device.  One PCG iteration
+// (Algorithm 1 with Algorithm 2) is a fixed sequence of kernels over all
+// solves of the batch; solves that have stopped leave every kernel at once.
+// Two iterations (the residual and direction buffers swap roles) are captured
+// in a CUDA graph that the host replays; the host reads the per-solve flags
+// only every `check_every` iterations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "gpsoc_internal.cuh"
+#include "kernels.cuh"
+
+using namespace gpsoc;
+
+namespace {
+
+thread_local std::string g_err;
+
+gpsoc_status fail(gpsoc_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(GPSOC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Records every kernel the host enqueues: counts launches and, when profiling,
+// brackets each with CUDA events on the problem's stream.
+struct Tracker {
+  cudaStream_t stream = nullptr;
+  uint64_t count = 0;
+  bool events = false;
+  std::vector<const char*> names;
+  std::vector<cudaEvent_t> evs;
+  void start() {
+    if (events) { cudaEvent_t e; cudaEventCreate(&e); cudaEventRecord(e, stream); evs.push_back(e); }
+  }
+  void mark(const char* name) {
+    ++count;
+    if (events) {
+      cudaEvent_t e; cudaEventCreate(&e); cudaEventRecord(e, stream); evs.push_back(e);
+      names.push_back(name);
+    }
+  }
+};
+
+template <class T>
+struct Bufs {
+  using C = cx_t<T>;
+  C *Phi = nullptr, *HPhi = nullptr, *R[2] = {nullptr, nullptr}, *P[2] = {nullptr, nullptr};
+  C *Z = nullptr, *D = nullptr, *A = nullptr, *B = nullptr, *W = nullptr, *G = nullptr;
+};
+
+
+const char* row_name(int m) {
+  static const char* n[] = {"row_fwd", "row_fwd_proj", "row_fwd_pre", "row_inv_h", "row_inv_p", "row_inv_pre",
+                            "row_inv_plain", "row_inv_lin"};
+  return n[m];
+}
+const char* col_name(int m, int axis) {
+  static const char* n[2][7] = {{"coly_fwd", "coly_inv", "coly_mid_h", "coly_mid_pre", "coly_ymid_h", "coly_yinv_h", "coly_kin"},
+                                {"colz_fwd", "colz_inv", "colz_mid_h", "colz_mid_pre", "colz_ymid_h", "colz_yinv_h", "colz_kin"}};
+  return n[axis == 2 ? 1 : 0][m];
+}
+const char* scalar_name(int ph) {
+  static const char* n[] = {"sc_init", "sc_obs", "sc_res", "sc_beta", "sc_cproj", "sc_step", "sc_cproj_reset",
+                            "sc_step_reset", "sc_norm", "sc_model"};
+  return n[ph];
+}
+const char* elem_name(int m) {
+  static const char* n[] = {"el_dir", "el_update", "el_mass", "el_scale"};
+  return n[m];
+}
+}  // namespace
+
+struct gpsoc_problem {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1};
+  int batch = 1;
+  gpsoc_trap trap{};
+  double* d_userV = nullptr;
+  std::vector<gpsoc_params> params;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  PhysDev* d_phys = nullptr;
+  SolveState* d_st = nullptr;
+  SolveState* h_st = nullptr;   // pinned mirror
+  double* d_part = nullptr;
+  int pmax = 0;
+  double* d_scale = nullptr;    // per-solve scale factors
+  double* d_tmp = nullptr;      // 3*batch doubles + model outputs
+  size_t tmp_len = 0;
+  Bufs<double> b64;
+  std::map<int, double2*> tw64;
+  int level = 0;
+  bool has_state = false;
+  int max_level = 0;
+  // captured iteration graph (two iterations) for the current level / options
+  cudaGraphExec_t graph = nullptr;
+  int graph_level = -1;
+  OptsDev graph_opts{};
+  uint64_t graph_kernels = 0;   // kernels per replay of the captured graph
+  uint64_t launches = 0;        // kernels launched so far (graph replays included)
+  Tracker* tr = nullptr;        // active tracker while enqueueing
+  std::vector<std::string> prof_names;
+};
+
+namespace {
+
+void mark(gpsoc_problem* p, const char* name) {
+  if (p->tr) p->tr->mark(name);
+  else p->launches++;
+}
+template <class T>
+void RL(gpsoc_problem* p, int mode, const ChainArgs<T>& a) {
+  launch_row<T>(mode, a, 0, Launch{}, p->stream);
+  mark(p, row_name(mode));
+}
+template <class T>
+void CL(gpsoc_problem* p, int mode, int axis, const ChainArgs<T>& a) {
+  launch_col<T>(mode, axis, a, Launch{}, p->stream);
+  mark(p, col_name(mode, axis));
+}
+void SL(gpsoc_problem* p, const ScalarArgs& x) {
+  SL(p, x);
+  mark(p, scalar_name(x.phase));
+}
+template <class T>
+void EL(gpsoc_problem* p, int mode, const ElemArgs<T>& e) {
+  launch_elem<T>(mode, e, p->stream);
+  mark(p, elem_name(mode));
+}
+
+Geo make_geo(const gpsoc_problem* p, int level) {
+  Geo g{};
+  g.d = p->dim;
+  g.npts = 1;
+  g.dV = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    if (i < p->dim) {
+      g.n[i] = p->n[i] >> level;
+      g.L[i] = p->L[i];
+      g.h[i] = 2.0 * p->L[i] / g.n[i];
+      g.dV *= g.h[i];
+    } else {
+      g.n[i] = 1;
+      g.L[i] = 1.0;
+      g.h[i] = 1.0;
+    }
+    g.log2n[i] = ilog2(g.n[i]);
+    g.npts *= g.n[i];
+  }
+  return g;
+}
+
+TrapDev make_trap(const gpsoc_problem* p, int level) {
+  TrapDev t{};
+  for (int i = 0; i < 3; ++i) t.half_g2[i] = (i < p->dim) ? 0.5 * p->trap.g[i] * p->trap.g[i] : 0.0;
+  t.quad = (p->trap.kind == GPSOC_TRAP_HARMONIC) ? 0.0 : p->trap.quad;
+  t.quart = (p->trap.kind == GPSOC_TRAP_HARMONIC) ? 0.0 : p->trap.quart;
+  t.userV = (level == 0) ? p->d_userV : nullptr;
+  return t;
+}
+
+gpsoc_status twiddles(gpsoc_problem* p, int n, const double2** out) {
+  auto it = p->tw64.find(n);
+  if (it != p->tw64.end()) { *out = it->second; return GPSOC_OK; }
+  std::vector<double2> h(n / 2);
+  const double PI = 3.14159265358979323846;
+  for (int k = 0; k < n / 2; ++k) {
+    const double ang = -2.0 * PI * (double)k / (double)n;
+    h[k] = make_double2(std::cos(ang), std::sin(ang));
+  }
+  double2* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(double2) * (n / 2 > 0 ? n / 2 : 1)));
+  CK(cudaMemcpy(d, h.data(), sizeof(double2) * (n / 2), cudaMemcpyHostToDevice));
+  p->tw64[n] = d;
+  *out = d;
+  return GPSOC_OK;
+}
+
+template <class T>
+gpsoc_status chain_args(gpsoc_problem* p, int level, ChainArgs<T>& a) {
+  a = ChainArgs<T>{};
+  a.g = make_geo(p, level);
+  a.trap = make_trap(p, level);
+  a.phys = p->d_phys;
+  a.st = p->d_st;
+  a.part = p->d_part;
+  a.pmax = p->pmax;
+  a.nsolve = p->batch;
+  a.gate = GATE_ACTIVE;
+  a.scale = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    if (i < p->dim) {
+      const double2* tw;
+      gpsoc_status s = twiddles(p, a.g.n[i], &tw);
+      if (s != GPSOC_OK) return s;
+      a.tw[i] = tw;
+    }
+  }
+  return GPSOC_OK;
+}
+
+ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
+  ScalarArgs s{};
+  s.st = p->d_st;
+  s.phys = p->d_phys;
+  s.part = p->d_part;
+  s.pmax = p->pmax;
+  Launch lc{};
+  s.nb_row = row_blocks_per_solve<double>(g, lc);
+  s.nb_col = col_blocks_per_solve<double>(g, p->dim - 1, lc);
+  s.nsolve = p->batch;
+  s.phase = phase;
+  s.npts = g.npts;
+  s.dV = g.dV;
+  s.norm_scale = p->d_scale;
+  (void)level;
+  return s;
+}
+
+template <class T>
+ElemArgs<T> elem_args(gpsoc_problem* p, const Geo& g, int gate) {
+  ElemArgs<T> e{};
+  e.st = p->d_st;
+  e.part = p->d_part;
+  e.pmax = p->pmax;
+  e.npts = g.npts;
+  e.bps = row_blocks_per_solve<double>(g, Launch{});
+  e.nsolve = p->batch;
+  e.gate = gate;
+  e.scalev = p->d_scale;
+  return e;
+}
+
+// H(Phi) chain: src -> dst (H(src) with nonlinear terms) and energy reductions
+template <class T>
+void run_h_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* src, cx_t<T>* dst) {
+  cudaStream_t st = p->stream;
+  Launch lc{};
+  a.in0 = src; a.out0 = B.A;
+  RL<T>(p, ROW_FWD_PLAIN, a);
+  if (p->dim == 2) {
+    a.in0 = B.A; a.out0 = B.W; a.out1 = B.G;
+    CL<T>(p, COL_YMID_H, 1, a);
+  } else {
+    a.in0 = B.A; a.out0 = B.B;
+    CL<T>(p, COL_FWD, 1, a);
+    a.in0 = B.B; a.out0 = B.B;
+    CL<T>(p, COL_MID_H, 2, a);
+    a.in0 = B.B; a.in1 = B.A; a.out0 = B.W; a.out1 = B.G;
+    CL<T>(p, COL_YINV_H, 1, a);
+  }
+  a.in0 = B.W; a.in1 = B.G; a.in2 = src; a.out0 = dst; a.out1 = nullptr;
+  RL<T>(p, ROW_INV_H, a);
+}
+
+// preconditioner chain: r = in0 - mu Phi (or in0 given as r) -> rout, z = P_C r -> zout
+template <class T>
+void run_pre_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* hphi, const cx_t<T>* phi,
+                   cx_t<T>* rout, const cx_t<T>* rprev, cx_t<T>* zout, bool res_phase, const ScalarArgs* sres) {
+  cudaStream_t st = p->stream;
+  Launch lc{};
+  a.in0 = hphi; a.in1 = phi; a.out0 = B.A; a.out1 = rout;
+  RL<T>(p, ROW_FWD_PRE, a);
+  if (res_phase && sres) SL(p, *sres);
+  a.given_r = 0;
+  if (p->dim == 2) {
+    a.in0 = B.A; a.out0 = B.A;
+    CL<T>(p, COL_MID_PRE, 1, a);
+  } else {
+    a.in0 = B.A; a.out0 = B.A;
+    CL<T>(p, COL_FWD, 1, a);
+    CL<T>(p, COL_MID_PRE, 2, a);
+    a.scale = 1.0;
+    CL<T>(p, COL_INV, 1, a);
+  }
+  a.in0 = B.A; a.in1 = phi; a.in2 = rout; a.in3 = rprev; a.out0 = zout;
+  RL<T>(p, ROW_INV_PRE, a);
+}
+
+// P chain: P = D - cproj Phi -> pout, step-model reductions
+template <class T>
+void run_p_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* D, const cx_t<T>* phi,
+                 const cx_t<T>* hphi, cx_t<T>* pout) {
+  cudaStream_t st = p->stream;
+  Launch lc{};
+  a.in0 = D; a.in1 = phi; a.out0 = B.A; a.out1 = pout;
+  RL<T>(p, ROW_FWD_PROJ, a);
+  if (p->dim == 2) {
+    a.in0 = B.A; a.out0 = B.W; a.out1 = B.G;
+    CL<T>(p, COL_YMID_H, 1, a);
+  } else {
+    a.in0 = B.A; a.out0 = B.B; a.out1 = nullptr;
+    CL<T>(p, COL_FWD, 1, a);
+    a.in0 = B.B; a.out0 = B.B;
+    CL<T>(p, COL_MID_H, 2, a);
+    a.in0 = B.B; a.in1 = B.A; a.out0 = B.W; a.out1 = B.G;
+    CL<T>(p, COL_YINV_H, 1, a);
+  }
+  a.in0 = B.W; a.in1 = B.G; a.in2 = pout; a.in3 = phi; a.in4 = hphi; a.out0 = nullptr; a.out1 = nullptr;
+  RL<T>(p, ROW_INV_P, a);
+}
+
+// One PCG iteration for all active solves (Algorithm 1 with Algorithm 2).
+template <class T>
+gpsoc_status enqueue_iteration(gpsoc_problem* p, int level, Bufs<T>& B, int parity, const OptsDev& o, int fp32) {
+  cudaStream_t st = p->stream;
+  ChainArgs<T> a;
+  gpsoc_status s = chain_args<T>(p, level, a);
+  if (s != GPSOC_OK) return s;
+  const Geo g = a.g;
+  auto sc = [&](int phase) {
+    ScalarArgs x = scalar_args(p, level, phase, g);
+    x.opts = o;
+    x.flags = fp32 ? 2 : 0;
+    SL(p, x);
+  };
+  const int cur = parity & 1, prv = cur ^ 1;
+  // H(Phi^n), E, mu, alpha
+  run_h_chain<T>(p, a, B, B.Phi, B.HPhi);
+  sc(PH_OBS);
+  // r^n, stopping test, P_C r^n
+  ScalarArgs sres = scalar_args(p, level, PH_RES, g);
+  sres.opts = o;
+  run_pre_chain<T>(p, a, B, B.HPhi, B.Phi, B.R[cur], B.R[prv], B.Z, true, &sres);
+  sc(PH_BETA);
+  // D^n, P^n, step model, Algorithm 2
+  for (int round = 0; round < 2; ++round) {
+    ElemArgs<T> e = elem_args<T>(p, g, round == 0 ? GATE_ACTIVE : GATE_RESET);
+    e.in0 = B.Z; e.in1 = B.P[prv]; e.in2 = B.Phi; e.out0 = B.D;
+    EL<T>(p, EL_DIR, e);
+    sc(round == 0 ? PH_CPROJ : PH_CPROJ_RESET);
+    ChainArgs<T> ap = a;
+    ap.gate = (round == 0) ? GATE_ACTIVE : GATE_RESET;
+    run_p_chain<T>(p, ap, B, B.D, B.Phi, B.HPhi, B.P[cur]);
+    sc(round == 0 ? PH_STEP : PH_STEP_RESET);
+  }
+  // Phi^{n+1}
+  ElemArgs<T> e = elem_args<T>(p, g, GATE_ACTIVE);
+  e.in0 = B.P[cur]; e.out0 = B.Phi;
+  EL<T>(p, EL_UPDATE, e);
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+OptsDev make_opts(const gpsoc_opts* o) {
+  OptsDev d{};
+  d.stop = o->stop ? o->stop : GPSOC_STOP_ENERGY;
+  d.tol = o->tol;
+  d.res_tol = o->res_tol;
+  d.max_iter = o->max_iter > 0 ? o->max_iter : 100000;
+  d.theta_trial = o->theta_trial > 0 ? o->theta_trial : 0.1;
+  d.sigma = (o->sigma > 0 && o->sigma < 1) ? o->sigma : 0.5;
+  d.max_halvings = o->max_halvings > 0 ? o->max_halvings : 40;
+  d.no_stop = 0;
+  return d;
+}
+
+gpsoc_status init_level(gpsoc_problem* p, int level, bool reset_counters) {
+  const Geo g = make_geo(p, level);
+  ScalarArgs x = scalar_args(p, level, PH_INIT, g);
+  x.flags = reset_counters ? 1 : 0;
+  SL(p, x);
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+gpsoc_status sync_state(gpsoc_problem* p) {
+  CK(cudaMemcpyAsync(p->h_st, p->d_st, sizeof(SolveState) * p->batch, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status build_graph(gpsoc_problem* p, int level, const OptsDev& o) {
+  if (p->graph && p->graph_level == level && std::memcmp(&p->graph_opts, &o, sizeof(o)) == 0) return GPSOC_OK;
+  if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+  cudaGraph_t gr;
+  Tracker tr;
+  tr.stream = p->stream;
+  p->tr = &tr;
+  CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  gpsoc_status s = enqueue_iteration<double>(p, level, p->b64, 0, o, 0);
+  if (s == GPSOC_OK) s = enqueue_iteration<double>(p, level, p->b64, 1, o, 0);
+  cudaError_t e = cudaStreamEndCapture(p->stream, &gr);
+  p->tr = nullptr;
+  p->graph_kernels = tr.count;
+  if (s != GPSOC_OK) { if (e == cudaSuccess) cudaGraphDestroy(gr); return s; }
+  if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  p->graph_level = level;
+  p->graph_opts = o;
+  return GPSOC_OK;
+}
+
+gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level) {
+  gpsoc_status s = init_level(p, level, first_level);
+  if (s != GPSOC_OK) return s;
+  s = build_graph(p, level, o);
+  if (s != GPSOC_OK) return s;
+  const int pairs = (check_every + 1) / 2;
+  const long long cap = (long long)o.max_iter + 4;
+  for (long long it = 0; it <= cap; it += 2 * pairs) {
+    for (int k = 0; k < pairs; ++k) {
+      CK(cudaGraphLaunch(p->graph, p->stream));
+      p->launches += p->graph_kernels;
+    }
+    s = sync_state(p);
+    if (s != GPSOC_OK) return s;
+    bool any = false;
+    for (int i = 0; i < p->batch; ++i) any |= (p->h_st[i].active != 0);
+    if (!any) return GPSOC_OK;
+  }
+  return GPSOC_OK;
+}
+
+gpsoc_status normalize(gpsoc_problem* p, int level) {
+  const Geo g = make_geo(p, level);
+  ElemArgs<double> e = elem_args<double>(p, g, GATE_ALL);
+  e.in0 = p->b64.Phi;
+  EL<double>(p, EL_MASS, e);
+  ScalarArgs x = scalar_args(p, level, PH_NORM, g);
+  SL(p, x);
+  e.in0 = p->b64.Phi; e.out0 = p->b64.Phi;
+  EL<double>(p, EL_SCALE, e);
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+gpsoc_status prolong_impl(gpsoc_problem* p, int level) {
+  // spectrum at level (coarse) -> zero padded at level-1 (fine) -> physical, x 2^d, renormalise
+  const Geo gc = make_geo(p, level), gf = make_geo(p, level - 1);
+  Bufs<double>& B = p->b64;
+  ChainArgs<double> a;
+  gpsoc_status s = chain_args<double>(p, level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  Launch lc{};
+  a.in0 = B.Phi; a.out0 = B.A;
+  RL<double>(p, ROW_FWD_PLAIN, a);
+  a.in0 = B.A; a.out0 = B.A;
+  for (int ax = 1; ax < p->dim; ++ax) CL<double>(p, COL_FWD, ax, a);
+  launch_pad<double>(B.A, B.W, gc, gf, p->batch, p->stream);
+  mark(p, "pad");
+  ChainArgs<double> f;
+  s = chain_args<double>(p, level - 1, f);
+  if (s != GPSOC_OK) return s;
+  f.gate = GATE_ALL;
+  f.in0 = B.W; f.out0 = B.W; f.scale = 1.0;
+  for (int ax = p->dim - 1; ax >= 1; --ax) CL<double>(p, COL_INV, ax, f);
+  f.in0 = B.W; f.out0 = B.Phi;
+  f.scale = (double)(1 << p->dim) / (double)gf.npts;   // 1/n_fine^d of the inverse, times 2^d
+  RL<double>(p, ROW_INV_PLAIN, f);
+  CK(cudaGetLastError());
+  s = normalize(p, level - 1);
+  if (s != GPSOC_OK) return s;
+  p->level = level - 1;
+  return GPSOC_OK;
+}
+
+void fill_results(const gpsoc_problem* p, gpsoc_result* r, int levels) {
+  for (int i = 0; i < p->batch; ++i) {
+    const SolveState& S = p->h_st[i];
+    gpsoc_result& o = r[i];
+    o.status = S.status;
+    if (S.status == GPSOC_OK && S.active) o.status = GPSOC_ENOTCONV;
+    o.iters = S.iters;
+    o.total_iters = S.total_iters;
+    o.levels = levels;
+    o.beta_resets = S.beta_resets;
+    o.halvings = S.halvings;
+    o.fp32_iters = S.fp32_iters;
+    o.fp64_iters = S.fp64_iters;
+    o.energy = S.E;
+    o.mu = S.mu;
+    for (int c = 0; c < 3; ++c) o.mass[c] = S.mass[c];
+    o.res_inf = S.res_inf;
+    o.dE_last = S.dE_last;
+  }
+}
+
+gpsoc_status check_problem(const gpsoc_problem* p) {
+  if (!p) return fail(GPSOC_EINVAL, "problem is NULL");
+  return GPSOC_OK;
+}
+
+gpsoc_status observables_now(gpsoc_problem* p) {
+  // H chain + observables for the current state without touching iteration flags
+  ChainArgs<double> a;
+  gpsoc_status s = chain_args<double>(p, p->level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  run_h_chain<double>(p, a, p->b64, p->b64.Phi, p->b64.HPhi);
+  ScalarArgs x = scalar_args(p, p->level, PH_OBS, a.g);
+  x.force = 1;
+  SL(p, x);
+  CK(cudaGetLastError());
+  return sync_state(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gpsoc_last_error(void) { return g_err.c_str(); }
+const char* gpsoc_version(void) { return "gpsoc 0.1 (sm_103a)"; }
+
+gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const gpsoc_params* params, int batch,
+                          void* cuda_stream, gpsoc_problem** out) {
+  g_err.clear();
+  if (!grid || !trap || !params || !out) return fail(GPSOC_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (grid->dim != 2 && grid->dim != 3) return fail(GPSOC_EINVAL, "dim must be 2 or 3");
+  if (batch < 1) return fail(GPSOC_EINVAL, "batch must be >= 1");
+  for (int i = 0; i < grid->dim; ++i) {
+    if (!pow2(grid->n[i]) || grid->n[i] < 8 || grid->n[i] > 1024)
+      return fail(GPSOC_EINVAL, "grid sizes must be powers of two in [8, 1024]");
+    if (!(grid->L[i] > 0) || !std::isfinite(grid->L[i])) return fail(GPSOC_EINVAL, "box half-widths must be > 0");
+  }
+  if (trap->kind < 0 || trap->kind > 2) return fail(GPSOC_EINVAL, "unknown trap kind");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(trap->g[i])) return fail(GPSOC_EINVAL, "trap frequencies must be finite");
+  if (!std::isfinite(trap->quad) || !std::isfinite(trap->quart)) return fail(GPSOC_EINVAL, "trap coefficients must be finite");
+  if (trap->kind == GPSOC_TRAP_USER && !trap->user_V) return fail(GPSOC_EINVAL, "user trap without user_V");
+  for (int b = 0; b < batch; ++b) {
+    const gpsoc_params& q = params[b];
+    if (!std::isfinite(q.Omega) || !std::isfinite(q.gamma) || !std::isfinite(q.beta0) || !std::isfinite(q.beta1))
+      return fail(GPSOC_EINVAL, "physical parameters must be finite");
+  }
+  gpsoc_problem* p = new gpsoc_problem();
+  p->dim = grid->dim;
+  for (int i = 0; i < 3; ++i) {
+    p->n[i] = (i < grid->dim) ? grid->n[i] : 1;
+    p->L[i] = (i < grid->dim) ? grid->L[i] : 1.0;
+  }
+  p->batch = batch;
+  p->trap = *trap;
+  p->trap.user_V = nullptr;
+  p->params.assign(params, params + batch);
+  int nmin = 1 << 30;
+  for (int i = 0; i < p->dim; ++i) nmin = std::min(nmin, p->n[i]);
+  p->max_level = ilog2(nmin) - 3;
+  auto bail = [&](gpsoc_status s, const std::string& m) { gpsoc_destroy(p); return fail(s, m); };
+  if (cuda_stream) {
+    p->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(GPSOC_ECUDA, "stream create failed");
+    p->own_stream = true;
+  }
+  if (chain_prepare<double>() != cudaSuccess || chain_prepare<float>() != cudaSuccess)
+    return bail(GPSOC_ECUDA, "kernel attribute setup failed (is a GB300 / sm_103 device current?)");
+  const Geo g = make_geo(p, 0);
+  const size_t arr = sizeof(double2) * (size_t)batch * 3 * g.npts;
+  double2** slots[] = {&p->b64.Phi, &p->b64.HPhi, &p->b64.R[0], &p->b64.R[1], &p->b64.P[0], &p->b64.P[1],
+                       &p->b64.Z, &p->b64.D, &p->b64.A, &p->b64.B, &p->b64.W, &p->b64.G};
+  for (double2** sl : slots) {
+    if (cudaMalloc(sl, arr) != cudaSuccess) { cudaGetLastError(); return bail(GPSOC_ENOMEM, "device allocation failed"); }
+  }
+  // partial-sum stride: the largest blocks-per-solve of any pass at the finest level
+  Launch lc{};
+  p->pmax = row_blocks_per_solve<double>(g, lc);
+  for (int ax = 1; ax < p->dim; ++ax) p->pmax = std::max(p->pmax, col_blocks_per_solve<double>(g, ax, lc));
+  if (cudaMalloc(&p->d_part, sizeof(double) * (size_t)batch * NSLOT * p->pmax) != cudaSuccess)
+    return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMalloc(&p->d_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMemset(p->d_st, 0, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ECUDA, "memset failed");
+  if (cudaMallocHost(&p->h_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "host allocation failed");
+  if (cudaMalloc(&p->d_scale, sizeof(double) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  p->tmp_len = (size_t)batch * 64 + 4096;
+  if (cudaMalloc(&p->d_tmp, sizeof(double) * p->tmp_len) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  std::vector<PhysDev> ph(batch);
+  for (int b = 0; b < batch; ++b) ph[b] = PhysDev{params[b].Omega, params[b].gamma, params[b].beta0, params[b].beta1};
+  if (cudaMalloc(&p->d_phys, sizeof(PhysDev) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMemcpy(p->d_phys, ph.data(), sizeof(PhysDev) * batch, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(GPSOC_ECUDA, "copy failed");
+  // twiddle tables of every axis length of every level (no allocation later, e.g. during graph capture)
+  for (int lev = 0; lev <= p->max_level; ++lev) {
+    for (int i = 0; i < p->dim; ++i) {
+      const double2* tw;
+      if (twiddles(p, p->n[i] >> lev, &tw) != GPSOC_OK) return bail(GPSOC_ENOMEM, "twiddle setup failed");
+    }
+  }
+  if (trap->kind == GPSOC_TRAP_USER) {
+    if (cudaMalloc(&p->d_userV, sizeof(double) * g.npts) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+    if (cudaMemcpy(p->d_userV, trap->user_V, sizeof(double) * g.npts, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(GPSOC_ECUDA, "copy failed");
+  }
+  *out = p;
+  return GPSOC_OK;
+}
+
+void gpsoc_destroy(gpsoc_problem* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  double2* arrs[] = {p->b64.Phi, p->b64.HPhi, p->b64.R[0], p->b64.R[1], p->b64.P[0], p->b64.P[1],
+                     p->b64.Z, p->b64.D, p->b64.A, p->b64.B, p->b64.W, p->b64.G};
+  for (double2* a : arrs) if (a) cudaFree(a);
+  for (auto& kv : p->tw64) cudaFree(kv.second);
+  if (p->d_part) cudaFree(p->d_part);
+  if (p->d_st) cudaFree(p->d_st);
+  if (p->h_st) cudaFreeHost(p->h_st);
+  if (p->d_scale) cudaFree(p->d_scale);
+  if (p->d_tmp) cudaFree(p->d_tmp);
+  if (p->d_phys) cudaFree(p->d_phys);
+  if (p->d_userV) cudaFree(p->d_userV);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+size_t gpsoc_solve_size(const gpsoc_problem* p, int level) {
+  if (!p || level < 0 || level > p->max_level) return 0;
+  return (size_t)3 * make_geo(p, level).npts;
+}
+
+gpsoc_status gpsoc_set_initial(gpsoc_problem* p, const double* psi, int level) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!psi) return fail(GPSOC_EINVAL, "psi is NULL");
+  if (level < 0 || level > p->max_level) return fail(GPSOC_EINVAL, "level out of range");
+  const Geo g = make_geo(p, level);
+  CK(cudaMemcpyAsync(p->b64.Phi, psi, sizeof(double2) * (size_t)p->batch * 3 * g.npts, cudaMemcpyHostToDevice, p->stream));
+  p->level = level;
+  gpsoc_status s = normalize(p, level);
+  if (s != GPSOC_OK) return s;
+  CK(cudaStreamSynchronize(p->stream));
+  p->has_state = true;
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_set_initial_device(gpsoc_problem* p, const void* dptr, int is_fp32, int level) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!dptr) return fail(GPSOC_EINVAL, "dptr is NULL");
+  if (level < 0 || level > p->max_level) return fail(GPSOC_EINVAL, "level out of range");
+  const Geo g = make_geo(p, level);
+  launch_convert<double>(dptr, is_fp32, p->b64.Phi, (long long)p->batch * 3 * g.npts, p->stream);
+  mark(p, "convert");
+  CK(cudaGetLastError());
+  p->level = level;
+  gpsoc_status s = normalize(p, level);
+  if (s != GPSOC_OK) return s;
+  CK(cudaStreamSynchronize(p->stream));
+  p->has_state = true;
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_set_initial_kind(gpsoc_problem* p, const int kind[3], int level) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!kind) return fail(GPSOC_EINVAL, "kind is NULL");
+  if (level < 0 || level > p->max_level) return fail(GPSOC_EINVAL, "level out of range");
+  for (int c = 0; c < 3; ++c) {
+    if (kind[c] < 0 || kind[c] > 9) return fail(GPSOC_EINVAL, "guess kind must be in 0..9");
+    if (kind[c] == 9) {
+      if (p->trap.kind != GPSOC_TRAP_HARMONIC) return fail(GPSOC_EINVAL, "guess (f) needs a harmonic trap");
+      for (int b = 0; b < p->batch; ++b)
+        if (!(p->params[b].beta0 > 0)) return fail(GPSOC_EINVAL, "guess (f) needs beta0 > 0");
+    }
+  }
+  const Geo g = make_geo(p, level);
+  const double PI = 3.14159265358979323846;
+  double base;
+  if (p->dim == 2) base = 0.5 * std::sqrt(4.0 * p->trap.g[0] * p->trap.g[1] / PI);
+  else base = 0.5 * std::pow(15.0 * p->trap.g[0] * p->trap.g[1] * p->trap.g[2] / (4.0 * PI), 0.4);
+  TrapDev t = make_trap(p, level);
+  launch_guess(p->b64.Phi, g, t, p->d_phys, p->batch, kind, base, p->d_tmp, p->stream);
+  p->launches += 3;
+  CK(cudaGetLastError());
+  p->level = level;
+  gpsoc_status s = normalize(p, level);
+  if (s != GPSOC_OK) return s;
+  CK(cudaStreamSynchronize(p->stream));
+  p->has_state = true;
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result* results) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!opts) return fail(GPSOC_EINVAL, "opts is NULL");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
+  if (opts->stop < 0 || opts->stop > 3) return fail(GPSOC_EINVAL, "unknown stopping criterion");
+  if (!(opts->tol > 0)) return fail(GPSOC_EINVAL, "tol must be > 0");
+  const int levels = opts->cm_levels > 0 ? opts->cm_levels : 1;
+  if (levels - 1 > p->max_level) return fail(GPSOC_EINVAL, "too many multigrid levels for this grid");
+  if (p->level != levels - 1) return fail(GPSOC_ESTATE, "initial guess is not on the coarsest multigrid level");
+  if (levels > 1 && p->d_userV) return fail(GPSOC_EINVAL, "user potentials support single-level solves only");
+  const OptsDev o = make_opts(opts);
+  const int check = opts->check_every > 0 ? opts->check_every : 16;
+  gpsoc_status s = GPSOC_OK;
+  for (int lev = levels - 1; lev >= 0; --lev) {
+    if (lev < p->level) {
+      s = prolong_impl(p, lev + 1);
+      if (s != GPSOC_OK) return s;
+    }
+    s = run_level(p, lev, o, check, lev == levels - 1);
+    if (s != GPSOC_OK) return s;
+  }
+  s = sync_state(p);
+  if (s != GPSOC_OK) return s;
+  std::vector<gpsoc_result> tmp(p->batch);
+  fill_results(p, tmp.data(), levels);
+  if (results) std::memcpy(results, tmp.data(), sizeof(gpsoc_result) * p->batch);
+  for (int i = 0; i < p->batch; ++i)
+    if (tmp[i].status != GPSOC_OK) return fail((gpsoc_status)tmp[i].status, "solve " + std::to_string(i) + " did not converge");
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int restart, gpsoc_result* results) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!opts || iters < 0) return fail(GPSOC_EINVAL, "bad arguments");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  OptsDev o = make_opts(opts);
+  o.no_stop = 1;
+  gpsoc_status s;
+  if (restart) {
+    s = init_level(p, p->level, true);
+    if (s != GPSOC_OK) return s;
+  }
+  for (int k = 0; k < iters; ++k) {
+    s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
+    if (s != GPSOC_OK) return s;
+  }
+  s = sync_state(p);
+  if (s != GPSOC_OK) return s;
+  if (results) fill_results(p, results, 1);
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_get_psi(const gpsoc_problem* p, double* psi_out) {
+  g_err.clear();
+  if (!p || !psi_out) return fail(GPSOC_EINVAL, "NULL argument");
+  const Geo g = make_geo(p, p->level);
+  CK(cudaMemcpyAsync(psi_out, p->b64.Phi, sizeof(double2) * (size_t)p->batch * 3 * g.npts, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_get_psi_device(const gpsoc_problem* p, void* dptr) {
+  g_err.clear();
+  if (!p || !dptr) return fail(GPSOC_EINVAL, "NULL argument");
+  const Geo g = make_geo(p, p->level);
+  CK(cudaMemcpyAsync(dptr, p->b64.Phi, sizeof(double2) * (size_t)p->batch * 3 * g.npts, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_get_observables(gpsoc_problem* p, double* E, double* mu, double* mass) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
+  gpsoc_status s = observables_now(p);
+  if (s != GPSOC_OK) return s;
+  for (int i = 0; i < p->batch; ++i) {
+    if (E) E[i] = p->h_st[i].E;
+    if (mu) mu[i] = p->h_st[i].mu;
+    if (mass) for (int c = 0; c < 3; ++c) mass[3 * i + c] = p->h_st[i].mass[c];
+  }
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_apply_h(gpsoc_problem* p, double* hpsi, double* obs) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
+  gpsoc_status s = observables_now(p);
+  if (s != GPSOC_OK) return s;
+  const Geo g = make_geo(p, p->level);
+  if (hpsi) {
+    CK(cudaMemcpyAsync(hpsi, p->b64.HPhi, sizeof(double2) * (size_t)p->batch * 3 * g.npts, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  if (obs) {
+    for (int i = 0; i < p->batch; ++i) {
+      const SolveState& S = p->h_st[i];
+      double* o = obs + 9 * i;
+      o[0] = S.E; o[1] = S.mu;
+      for (int c = 0; c < 3; ++c) { o[2 + c] = S.alpha[c]; o[5 + c] = S.mass[c]; }
+      o[8] = S.Q;
+    }
+  }
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, const double* r, double* out) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!r || !out) return fail(GPSOC_EINVAL, "NULL argument");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
+  gpsoc_status s = observables_now(p);
+  if (s != GPSOC_OK) return s;
+  const Geo g = make_geo(p, p->level);
+  const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
+  Bufs<double>& B = p->b64;
+  CK(cudaMemcpyAsync(B.D, r, bytes, cudaMemcpyHostToDevice, p->stream));
+  ChainArgs<double> a;
+  s = chain_args<double>(p, p->level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  a.given_r = 1;
+  run_pre_chain<double>(p, a, B, B.D, B.Phi, B.R[0], nullptr, B.Z, false, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, B.Z, bytes, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* theta, int n_theta, double* out) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!P || !out || n_theta < 0 || (n_theta > 0 && !theta)) return fail(GPSOC_EINVAL, "bad arguments");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
+  if ((size_t)p->batch * (2 + n_theta) + n_theta > p->tmp_len) return fail(GPSOC_EINVAL, "too many angles");
+  gpsoc_status s = observables_now(p);
+  if (s != GPSOC_OK) return s;
+  const Geo g = make_geo(p, p->level);
+  const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
+  Bufs<double>& B = p->b64;
+  CK(cudaMemcpyAsync(B.D, P, bytes, cudaMemcpyHostToDevice, p->stream));
+  double* d_theta = p->d_tmp;
+  double* d_out = p->d_tmp + n_theta;
+  if (n_theta) CK(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, p->stream));
+  // cproj = 0 so that P is used as given
+  for (int i = 0; i < p->batch; ++i) p->h_st[i].cproj = 0.0;
+  CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
+  ChainArgs<double> a;
+  s = chain_args<double>(p, p->level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  run_p_chain<double>(p, a, B, B.D, B.Phi, B.HPhi, B.P[0]);
+  ScalarArgs x = scalar_args(p, p->level, PH_MODEL, g);
+  x.force = 1;
+  x.thetas = d_theta;
+  x.n_theta = n_theta;
+  x.model_out = d_out;
+  SL(p, x);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, d_out, sizeof(double) * (size_t)p->batch * (2 + n_theta), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_prolong(gpsoc_problem* p, int level) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
+  if (level < 1 || level > p->max_level || level != p->level) return fail(GPSOC_EINVAL, "level must be the current level and >= 1");
+  gpsoc_status s = prolong_impl(p, level);
+  if (s != GPSOC_OK) return s;
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, double* ms, int cap, int* n_kernels) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!opts || iters < 1 || !ms || !n_kernels) return fail(GPSOC_EINVAL, "bad arguments");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  OptsDev o = make_opts(opts);
+  o.no_stop = 1;
+  gpsoc_status s = init_level(p, p->level, true);
+  if (s != GPSOC_OK) return s;
+  Tracker tr;
+  tr.stream = p->stream;
+  tr.events = true;
+  p->tr = &tr;
+  size_t per = 0;
+  std::vector<size_t> starts;
+  for (int k = 0; k < iters && s == GPSOC_OK; ++k) {
+    starts.push_back(tr.evs.size());
+    tr.start();
+    s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
+  }
+  p->tr = nullptr;
+  p->launches += tr.count;
+  if (s == GPSOC_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) s = fail(GPSOC_ECUDA, "profile sync failed");
+  if (s == GPSOC_OK) {
+    per = tr.names.size() / iters;
+    *n_kernels = (int)per;
+    p->prof_names.assign(tr.names.begin(), tr.names.begin() + per);
+    for (size_t k = 0; k < per && (int)k < cap; ++k) {
+      double acc = 0.0;
+      for (int it = 0; it < iters; ++it) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, tr.evs[starts[it] + k], tr.evs[starts[it] + k + 1]);
+        acc += t;
+      }
+      ms[k] = acc / iters;
+    }
+  }
+  for (cudaEvent_t e : tr.evs) cudaEventDestroy(e);
+  return s;
+}
+
+const char* gpsoc_profile_name(const gpsoc_problem* p, int k) {
+  if (!p || k < 0 || k >= (int)p->prof_names.size()) return "";
+  return p->prof_names[k].c_str();
+}
+
+uint64_t gpsoc_kernel_launches(const gpsoc_problem* p) { return p ? p->launches : 0; }
+
+gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, int inverse) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!data || count < 1 || axis < 0 || axis >= p->dim) return fail(GPSOC_EINVAL, "bad arguments");
+  if (count % 3 != 0 || count / 3 > p->batch) return fail(GPSOC_EINVAL, "count must be 3 * k with k <= batch");
+  ChainArgs<double> a;
+  gpsoc_status s = chain_args<double>(p, 0, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  a.nsolve = count / 3;
+  double2* d = (double2*)data;
+  Launch lc{};
+  const double sc = inverse ? 1.0 / a.g.n[axis] : 1.0;
+  a.in0 = d; a.out0 = d; a.scale = sc;
+  if (axis == 0) RL<double>(p, inverse ? ROW_INV_PLAIN : ROW_FWD_PLAIN, a);
+  else CL<double>(p, inverse ? COL_INV : COL_FWD, axis, a);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+}  // extern "C"

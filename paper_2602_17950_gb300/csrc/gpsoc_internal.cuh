@@ -1,0 +1,288 @@
+// Internal declarations shared by the CUDA translation units of libgpsoc.
+//
+// Data layout in device memory (one "3-array"): [solve][component][z][y][x],
+// x fastest, complex values interleaved (double2 or float2).  Component index
+// 0, 1, 2 holds phi_1, phi_0, phi_-1.
+//
+// Spectral conventions (Section 3.2 of arXiv 2602.17950): forward DFT along an
+// axis is unnormalised, exp(-2 pi i k m / n); coefficient index k stands for
+// p = k (k < n/2) or k - n (k >= n/2); wavenumber v = pi p / L.  The Nyquist
+// index k = n/2 keeps v = -pi n / (2L) in every symbol, odd ones included.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gpsoc.h"
+
+namespace gpsoc {
+
+// ------------------------------------------------------------------ complex helpers
+template <class T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+template <class T> using cx_t = typename Cx<T>::type;
+
+template <class C> __host__ __device__ __forceinline__ C mk(double re, double im) {
+  C c; c.x = (decltype(c.x))re; c.y = (decltype(c.y))im; return c;
+}
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <class C, class S> __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+
+// ------------------------------------------------------------------ geometry and parameters
+struct Geo {
+  int d;            // 2 or 3
+  int n[3];         // nx, ny, nz (nz = 1 in 2D)
+  int log2n[3];
+  double L[3], h[3];
+  long long npts;   // points of one component
+  double dV;        // h^d
+};
+
+struct TrapDev {
+  double half_g2[3];   // g_i^2 / 2
+  double quad, quart;
+  const double* userV; // npts doubles of the current level or nullptr
+};
+
+struct PhysDev { double Omega, gamma, c0, c1; };
+
+// Per-solve scalar state of the PCG iteration (device resident).
+struct SolveState {
+  int active;       // iterating
+  int status;       // gpsoc_status
+  int iters;        // accepted steps on this level
+  int total_iters;
+  int first;        // next iteration starts with beta = 0
+  int reset;        // Algorithm 2 Step 2 asked for beta = 0 in this iteration
+  int beta_resets, halvings;
+  int fp32_iters, fp64_iters;
+  int pad0, pad1;
+  // observables of the current iterate
+  double E, mu, Q;          // energy, chemical potential, <H_lin Phi, Phi>
+  double rho2, F2;          // sum rho^2, sum |F|^2 (times dV)
+  double alpha[3], mass[3];
+  double res_inf, dphi_inf;
+  // PCG scalars
+  double s_prev, s_cur, beta, cproj;
+  double P2, HPP, HPhiP, RPhi;
+  double I[6], J[6];
+  double a, b, theta, dE, dE_last;
+  double upd_c, upd_s, upd_scale;
+};
+
+struct OptsDev {
+  int stop;
+  double tol, res_tol;
+  int max_iter;
+  double theta_trial, sigma;
+  int max_halvings;
+  int no_stop;      // gpsoc_iterate: run without stopping tests
+};
+
+// reduction slots (per solve); partial sums live in part[(s * NSLOT + slot) * pmax + block]
+enum Slot {
+  SL_KIN0 = 0, SL_KIN1, SL_KIN2,                 // sum 1/2 |k|^2 |phat_l|^2
+  SL_Q, SL_RHO2, SL_F2,                           // <H_lin phi, phi>, sum rho^2, sum |F|^2
+  SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2,       // sum V|phi_l|^2, sum rho |phi_l|^2
+  SL_M0, SL_M1, SL_M2,                            // masses
+  SL_RINF,                                        // max |r|
+  SL_RZ, SL_RPZ,                                  // Re<r, z>, Re<r_prev, z>
+  SL_DPHI,                                        // Re<D, Phi>
+  SL_P2,                                          // ||P||^2
+  SL_HPP, SL_HPHIP, SL_RPHI,                      // <H_lin P,P>, Re<H Phi, P>, Re<P, Phi>
+  SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,         // rho cross integrals
+  SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP,         // spin cross integrals
+  SL_DPHIINF,                                     // max |Phi_new - Phi|
+  SL_NORM,                                        // sum |phi|^2 for normalisation
+  NSLOT
+};
+
+// gate of a chain kernel: which per-solve flag must be set for the block to run
+enum Gate { GATE_ALL = 0, GATE_ACTIVE = 1, GATE_RESET = 2 };
+
+template <class T>
+struct ChainArgs {
+  using C = cx_t<T>;
+  Geo g;
+  TrapDev trap;
+  const PhysDev* phys;
+  SolveState* st;
+  const C* in0; const C* in1; const C* in2; const C* in3; const C* in4;
+  C* out0; C* out1;
+  double* part; int pmax;
+  const C* tw[3];     // twiddle tables exp(-2 pi i k / n_axis), k < n_axis/2
+  int gate;
+  int nsolve;
+  double scale;       // extra scale factor (prolongation, normalisation)
+  int given_r;        // ROW_FWD_PRE: in0 already holds r (mu taken as 0)
+};
+
+__device__ __forceinline__ bool gate_ok(const SolveState* st, int gate, int s) {
+  if (gate == GATE_ALL) return true;
+  if (gate == GATE_ACTIVE) return st[s].active != 0;
+  return st[s].active != 0 && st[s].reset != 0;
+}
+
+// wavenumber of FFT index k on an axis of n points and half-width L
+__device__ __forceinline__ double wavenum(int k, int n, double L) {
+  int p = (k < (n >> 1)) ? k : k - n;
+  return 3.14159265358979323846 * (double)p / L;
+}
+
+__device__ __forceinline__ double trap_value(const TrapDev& t, const Geo& g, int ix, int iy, int iz,
+                                             long long idx) {
+  double x = -g.L[0] + ix * g.h[0];
+  double y = -g.L[1] + iy * g.h[1];
+  double v = t.half_g2[0] * x * x + t.half_g2[1] * y * y;
+  double r2 = x * x + y * y;
+  if (g.d == 3) {
+    double z = -g.L[2] + iz * g.h[2];
+    v += t.half_g2[2] * z * z;
+    r2 += z * z;
+  }
+  v += t.quad * r2 + t.quart * r2 * r2;
+  if (t.userV) v += t.userV[idx];
+  return v;
+}
+
+// ------------------------------------------------------------------ block reductions (deterministic)
+// Sums K doubles over the block in a fixed order: warp shuffle tree, then warps
+// in index order.  scratch: >= 32 * K doubles of shared memory.  Result valid in
+// thread 0.  IS_MAX selects max instead of sum.
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, const bool (&is_max)[K]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_down_sync(0xffffffffu, v[k], off);
+      v[k] = is_max[k] ? fmax(v[k], o) : v[k] + o;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double acc = scratch[k];
+      for (int w = 1; w < nw; ++w) acc = is_max[k] ? fmax(acc, scratch[w * K + k]) : acc + scratch[w * K + k];
+      v[k] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ shared-memory FFT
+// Radix-2 FFTs of nseq sequences of length 2^L held in shared memory.  Element e
+// of sequence q is at buf[(q / qgroup) * gstride + (q % qgroup) * qstride + e * estride].
+// tw[k] = exp(-2 pi i k / 2^L), k < 2^(L-1); inverse = conjugate twiddles (no 1/n).
+// fft_dit: bit-reversed input -> natural output (decimation in time).
+// fft_dif: natural input -> bit-reversed output (decimation in frequency).
+// SEQ_FAST: consecutive threads take consecutive sequences (column tiles)
+// instead of consecutive butterflies of one sequence (rows).
+template <class C, bool SEQ_FAST>
+__device__ __forceinline__ void fft_dit(C* buf, int L, int nseq, int qgroup, int gstride, int qstride,
+                                        int estride, const C* tw, bool inverse) {
+  const int half = 1 << (L - 1);
+  const int total = nseq * half;
+  for (int st = 0; st < L; ++st) {
+    const int m = 1 << st;
+    const int tws = L - 1 - st;  // twiddle index = pos << tws
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      int q, j;
+      if (SEQ_FAST) { q = b % nseq; j = b / nseq; }
+      else { q = b >> (L - 1); j = b & (half - 1); }
+      const int pos = j & (m - 1);
+      const int i0 = ((j >> st) << (st + 1)) + pos;
+      C* base = buf + (q / qgroup) * gstride + (q % qgroup) * qstride;
+      C w = tw[pos << tws];
+      if (inverse) w.y = -w.y;
+      C u = base[i0 * estride];
+      C t = cmul(w, base[(i0 + m) * estride]);
+      base[i0 * estride] = cadd(u, t);
+      base[(i0 + m) * estride] = csub(u, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <class C, bool SEQ_FAST>
+__device__ __forceinline__ void fft_dif(C* buf, int L, int nseq, int qgroup, int gstride, int qstride,
+                                        int estride, const C* tw, bool inverse) {
+  const int half = 1 << (L - 1);
+  const int total = nseq * half;
+  for (int st = L - 1; st >= 0; --st) {
+    const int m = 1 << st;
+    const int tws = L - 1 - st;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      int q, j;
+      if (SEQ_FAST) { q = b % nseq; j = b / nseq; }
+      else { q = b >> (L - 1); j = b & (half - 1); }
+      const int pos = j & (m - 1);
+      const int i0 = ((j >> st) << (st + 1)) + pos;
+      C* base = buf + (q / qgroup) * gstride + (q % qgroup) * qstride;
+      C w = tw[pos << tws];
+      if (inverse) w.y = -w.y;
+      C u = base[i0 * estride];
+      C v = base[(i0 + m) * estride];
+      base[i0 * estride] = cadd(u, v);
+      base[(i0 + m) * estride] = cmul(csub(u, v), w);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int j, int L) { return (int)(__brev((unsigned)j) >> (32 - L)); }
+
+// ------------------------------------------------------------------ host-side launch helpers
+struct Launch {
+  int rows_per_block;   // row passes
+  int cols_per_tile[3]; // column passes per axis
+  int threads;
+};
+
+template <class T> struct Chain;  // kernels of one precision (defined in chain.cu)
+
+// Launchers implemented in chain.cu (explicitly instantiated for double, float).
+enum RowMode {
+  ROW_FWD_PLAIN = 0,   // out0 = F_x(in0)
+  ROW_FWD_PROJ,        // P = in0 - cproj * in1 -> out1; out0 = F_x(P); reduce ||P||^2
+  ROW_FWD_PRE,         // r = in0 - mu in1 -> out1; out0 = F_x(s * r); reduce max|r|
+  ROW_INV_H,           // out0 = H(Phi) from T' (in0), G (in1), Phi (in2); energy reductions
+  ROW_INV_P,           // reductions of the step model from T' (in0), G (in1), P (in2), Phi (in3), HPhi (in4)
+  ROW_INV_PRE,         // z = s * F_x^-1(in0)/npts -> out0; reduce <r,z>, <r_prev,z> (in2 = r, in3 = r_prev, in1 = Phi)
+  ROW_INV_PLAIN,       // out0 = scale * F_x^-1(in0)
+  ROW_INV_LIN          // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
+};
+enum ColMode {
+  COL_FWD = 0,         // out0 = F_axis(in0)
+  COL_INV,             // out0 = F_axis^-1(in0) (unnormalised)
+  COL_MID_H,           // last axis, H chain: out0 = F^-1[M(k) F in0], reduce kinetic per component
+  COL_MID_PRE,         // last axis, preconditioner: out0 = F^-1[F in0 / (alpha_l + |k|^2/2)]
+  COL_YMID_H,          // 2D y pass of the H chain: out0 = T', out1 = G
+  COL_YINV_H,          // 3D y inverse pass of the H chain: in0 = C, in1 = A -> out0 = T', out1 = G
+  COL_MID_KIN          // last axis: reduce kinetic per component only (no output)
+};
+
+template <class T>
+void launch_row(int mode, const ChainArgs<T>& a, int nblocks_total, const Launch& lc, cudaStream_t s);
+template <class T>
+void launch_col(int mode, int axis, const ChainArgs<T>& a, const Launch& lc, cudaStream_t s);
+template <class T>
+int row_blocks_per_solve(const Geo& g, const Launch& lc);
+template <class T>
+int col_blocks_per_solve(const Geo& g, int axis, const Launch& lc);
+template <class T>
+cudaError_t chain_prepare();   // sets max dynamic shared memory attributes
+
+}  // namespace gpsoc

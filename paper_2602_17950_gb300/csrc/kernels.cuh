@@ -1,0 +1,61 @@
+// Argument blocks and launchers of the scalar and elementwise kernels (pcg.cu).
+#pragma once
+
+#include "gpsoc_internal.cuh"
+
+namespace gpsoc {
+
+enum Phase {
+  PH_INIT = 0,      // reset per-level flags (flags & 1: also reset counters)
+  PH_OBS,           // E, mu, alpha, masses from the H-chain partials
+  PH_RES,           // max |r| and the stopping test
+  PH_BETA,          // Polak-Ribiere+ beta
+  PH_CPROJ,         // Re<D, Phi>
+  PH_STEP,          // Algorithm 2 (step model, reset decision, backtracking, update coefficients)
+  PH_CPROJ_RESET,   // as PH_CPROJ / PH_STEP for solves in the beta = 0 re-run
+  PH_STEP_RESET,
+  PH_NORM,          // 1/sqrt(mass) per solve into norm_scale
+  PH_MODEL          // a_n, b_n and E(theta) - E(0) at given angles into model_out
+};
+
+struct ScalarArgs {
+  SolveState* st;
+  const PhysDev* phys;
+  const double* part;
+  int pmax;
+  int nb_row, nb_col;
+  int nsolve;
+  int phase;
+  int flags;          // PH_INIT: 1 = reset counters; PH_STEP: 2 = count as an FP32 iteration
+  long long npts;
+  double dV;
+  OptsDev opts;
+  double* norm_scale;
+  int force;          // process every solve regardless of its active flag
+  const double* thetas; int n_theta; double* model_out;
+};
+
+enum ElemMode { EL_DIR = 0, EL_UPDATE, EL_MASS, EL_SCALE };
+
+template <class T>
+struct ElemArgs {
+  using C = cx_t<T>;
+  const SolveState* st;
+  const C* in0; const C* in1; const C* in2;
+  C* out0;
+  double* part; int pmax;
+  const double* scalev;
+  long long npts;
+  int bps;            // blocks per solve (divides npts)
+  int nsolve;
+  int gate;
+};
+
+void launch_scalar(const ScalarArgs& a, cudaStream_t st);
+template <class T> void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st);
+template <class T> void launch_pad(const cx_t<T>* in, cx_t<T>* out, const Geo& gc, const Geo& gf, int nsolve, cudaStream_t st);
+template <class T> void launch_convert(const void* in, int in_fp32, cx_t<T>* out, long long count, cudaStream_t st);
+void launch_guess(double2* out, const Geo& g, const TrapDev& trap, const PhysDev* phys, int nsolve, const int kind[3],
+                  double muTF_base, double* mass_tmp, cudaStream_t st);
+
+}  // namespace gpsoc
