@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: ground-state solves per second of the cascadic-multigrid PCG
+solver on a GB300, plus p50/p99 solve latency.
+
+Workload (one step = one full solve, all steps of the method): 2D, 512x512 on
+[-16,16]^2, cascadic multigrid 128 -> 256 -> 512 by spectral zero padding,
+harmonic trap, Omega = 0.9, gamma = 1, beta0 = 1000, beta1 = -5, seeded
+vortex-phase initial guess, stop when the accepted step changes the energy by
+less than 1e-12.  FP64 arithmetic (`--precision fp64`, the default) or FP32
+transforms with FP64 reductions and FP64 polishing (`--precision mixed`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own seeded problem on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on this machine's host cores on
+a bounded sample of the same workload (see `cpu_sample`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import seeded_inputs as si  # noqa: E402
+
+METRIC = "ground-state solves/s & p50/p99 latency vs plain FP64 PCG, same energy tol"
+N_FINE = (512, 512)
+L_BOX = (16.0, 16.0)
+LEVELS = 3
+PAR = (0.9, 1.0, 1000.0, -5.0)
+TOL = 1e-12
+WORKLOAD = ("2D CM-PCG 128->256->512, 512x512 on [-16,16]^2, harmonic trap, Omega=0.9, gamma=1, "
+            "beta0=1000, beta1=-5, seeded vortex-phase guess, stop |dE|<1e-12")
+L2_BYTES = 256 << 20
+
+
+def coarse_shape():
+    return tuple(k >> (LEVELS - 1) for k in N_FINE)
+
+
+def initial_guess(rank: int) -> np.ndarray:
+    return si.gaussian_guess(coarse_shape(), L_BOX, si.seed_for(2, rank), vortex=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+def fft_flops(n: int) -> float:
+    """Standard operation count of a length-n complex radix-2 FFT: 5 n log2 n."""
+    return 5.0 * n * math.log2(n)
+
+
+def kernel_flops(name: str, n=N_FINE) -> float:
+    """Algorithmic FP64 flops of one launch of a 2D pass on one solve (3 components):
+    the FFTs it performs (5 n log2 n each); pointwise work is not counted."""
+    nx, ny = n
+    per_row = fft_flops(nx) * ny          # one transform of every row of one component
+    per_col = fft_flops(ny) * nx
+    table = {
+        "row_fwd": 1 * per_row, "row_fwd_proj": 1 * per_row, "row_fwd_pre": 1 * per_row,
+        "row_inv_h": 2 * per_row, "row_inv_p": 2 * per_row, "row_inv_pre": 1 * per_row,
+        "coly_ymid_h": 3 * per_col, "coly_mid_pre": 2 * per_col,
+    }
+    return 3.0 * table.get(name, 0.0)
+
+
+def kernel_bytes(name: str, n=N_FINE, elem=16) -> float:
+    """Algorithmic DRAM bytes of one launch of a 2D pass on one solve: 3-component
+    arrays read and written once each (elem = bytes per complex value)."""
+    arr = 3.0 * n[0] * n[1] * elem
+    rw = {"row_fwd": 2, "row_fwd_proj": 4, "row_fwd_pre": 4, "row_inv_h": 4, "row_inv_p": 5, "row_inv_pre": 5,
+          "coly_ymid_h": 4, "coly_mid_pre": 2, "el_dir": 4, "el_update": 3}
+    return arr * rw.get(name, 0)
+
+
+# ------------------------------------------------------------------ oracle (CPU) sample
+def oracle_sample(iters_per_level, budget_s: float = 20.0):
+    """Time the FP64 CPU oracle's PCG iterations on each level of the workload and
+    scale by the iteration counts of a full solve.  Returns (seconds per solve,
+    description of the sample)."""
+    from oracle.model import Grid, Model, Trap
+    from oracle.pcg import Options, pcg
+    psi = initial_guess(0)
+    per_iter = []
+    desc = []
+    for lev, its in enumerate(iters_per_level):
+        n = tuple(k >> (LEVELS - 1 - lev) for k in N_FINE)
+        m = Model(Grid(n, L_BOX), Trap(), Omega=PAR[0], gamma=PAR[1], c0=PAR[2], c1=PAR[3])
+        if lev > 0:
+            psi = np.stack([np.kron(psi[c], np.ones((2, 2))) for c in range(3)])  # any state of the right size
+        k = {0: 8, 1: 3, 2: 2}[lev]
+        t0 = time.perf_counter()
+        pcg(m, psi, Options(tol=1e-300, max_iter=k))
+        dt = (time.perf_counter() - t0) / (k + 1)       # k iterations plus the final H evaluation
+        per_iter.append(dt)
+        desc.append(f"{n[0]}^2: {k} its, {dt * 1e3:.0f} ms/it")
+    total = sum(t * i for t, i in zip(per_iter, iters_per_level))
+    return total, ("oracle PCG iterations timed per level (" + "; ".join(desc) + ") x the per-level iteration "
+                   f"counts of one solve {list(iters_per_level)}")
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    from paper_2602_17950_gb300.gpsoc import probe_peaks
+
+    build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    prec = 1 if args.precision == "mixed" else 0
+    psi0 = initial_guess(rank)
+    d_psi0 = torch.from_numpy(psi0[None].copy()).to(dev)
+    flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
+    prob = Problem(N_FINE, L_BOX, [PAR])
+    opts = dict(precision=prec, tol=TOL, cm_levels=LEVELS, check_every=32)
+
+    def step():
+        prob.set_initial_device(d_psi0.data_ptr(), level=LEVELS - 1)
+        return prob.solve(**opts)[0]
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    lat = []
+    results = []
+    launches0 = prob.kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        t_begin = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step()
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+            results.append(res)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_begin
+    launches = prob.kernel_launches() - launches0
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    total_ms = sum(lat)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    max_total_ms = float(t.item())
+    ok = all(r["status"] == "OK" for r in results)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    h_in = torch.empty(psi0[None].shape, dtype=torch.complex128, pin_memory=True)
+    h_in.numpy()[...] = psi0[None]
+    h_out = torch.empty((1, 3) + tuple(N_FINE[::-1]), dtype=torch.complex128, pin_memory=True)
+    e2e = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.set_initial(h_in.numpy(), level=LEVELS - 1)
+        r = prob.solve(**opts)[0]
+        prob.psi(out=h_out.numpy())
+        e2e.append(time.perf_counter() - t0)
+        ok = ok and r["status"] == "OK"
+
+    # per-kernel durations (CUDA events on the solver's stream) on the finest grid
+    prob.set_initial(si.gaussian_guess(N_FINE, L_BOX, si.seed_for(2, rank), vortex=True)[None], level=0)
+    prof = prob.profile(iters=10, precision=prec, tol=TOL)
+    fp64_peak, fp32_peak = probe_peaks()
+    prob.close()
+
+    if rank != 0:
+        return None
+    iters = results[-1]
+    total_it = sum(ms for _, ms in prof)
+    dom_name, dom_ms = max(prof, key=lambda kv: kv[1])
+    flops = kernel_flops(dom_name)
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    ms_per_step = max_total_ms / args.steps
+    value = world * 1000.0 / ms_per_step
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = None
+    if os.path.exists(peaks_file):
+        hbm_peak = json.load(open(peaks_file)).get("hbm_gbs")
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "solves_per_step_per_gpu": 1,
+                   "grid": "512x512", "levels": [128, 256, 512], "precision": args.precision,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak > 0 else None,
+                     "traffic": None, "peak_source": "FP64 FMA-chain probe (gpsoc_probe_peaks), this run",
+                     "share_of_iteration": dom_ms / total_it, "ms_per_launch": dom_ms,
+                     "algorithmic_flops_per_launch": flops},
+        "kernels_ms_per_iteration_512": {k: round(v, 5) for k, v in prof},
+        "solve": {"status_ok": ok, "energy": iters["energy"], "mu": iters["mu"], "iters_finest": iters["iters"],
+                  "iters_total": iters["total_iters"], "level_iters": iters["level_iters"],
+                  "beta_resets": iters["beta_resets"],
+                  "halvings": iters["halvings"]},
+        "e2e": {"value": 1.0 / statistics.mean(e2e), "unit": "solves/s",
+                "h2d_bytes_per_step": int(h_in.numpy().nbytes), "d2h_bytes_per_step": int(h_out.numpy().nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "peaks": {"fp64_tflops_probe": fp64_peak, "fp32_tflops_probe": fp32_peak, "hbm_gbs_measured": hbm_peak},
+    }
+    return out, results[-1]
+
+
+def per_level_iters(res_dict, n_levels):
+    """Iterations of one solve on each multigrid level (coarsest first)."""
+    return [int(v) for v in res_dict["level_iters"][:n_levels]]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # iteration counts of one solve from the GPU path (untimed), then the oracle's per-level cost
+        iters_lv = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                from paper_2602_17950_gb300 import Problem
+                from paper_2602_17950_gb300.build import build
+                build()
+                with Problem(N_FINE, L_BOX, [PAR]) as p:
+                    p.set_initial(initial_guess(0)[None], level=LEVELS - 1)
+                    r = p.solve(tol=TOL, cm_levels=LEVELS)[0]
+                iters_lv = per_level_iters(r, LEVELS)
+        except Exception:
+            iters_lv = None
+        if iters_lv is None:
+            iters_lv = [1000.0, 300.0, 300.0]
+        times = []
+        desc = ""
+        oracle_sample(iters_lv)                 # one untimed warm-up sample (pages in numpy)
+        for _ in range(args.steps):
+            t, desc = oracle_sample(iters_lv)
+            times.append(t)
+        v = 1.0 / statistics.mean(times)
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": 1, "grid": "512x512",
+                                               "levels": [128, 256, 512], "precision": "fp64"},
+               "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+               "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    got = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+    if rank != 0 or got is None:
+        return
+    out, last = got
+    if not args.no_cpu and world == 1:
+        t, desc = oracle_sample(per_level_iters(last, LEVELS))
+        out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

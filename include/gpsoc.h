@@ -91,7 +91,11 @@ typedef struct {
  *   cm_levels    1 = plain PCG on the grid; k > 1 = Algorithm 3 starting on the
  *                grid coarsened by 2^(k-1) per axis (the initial guess must then
  *                be given on that coarsest grid).
- *   check_every  iterations run between host convergence checks (0 = 16). */
+ *   check_every  iterations run between host convergence checks (0 = 16).
+ *   fp32_switch  GPSOC_MIXED only: the FP32 phase of each level ends when an
+ *                accepted step changes the energy by less than
+ *                tol + fp32_switch * |E| (or when no decrease is found);
+ *                0 selects 1e-11. */
 typedef struct {
   int precision;
   int stop;
@@ -102,11 +106,13 @@ typedef struct {
   int max_halvings;
   int cm_levels;
   int check_every;
+  double fp32_switch;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;
  * res_inf = max_l ||r_l||_inf of that iterate; dE_last = energy change of the
- * last accepted step. */
+ * last accepted step; level_iters[k] = iterations on multigrid level k
+ * (k = 0 the coarsest, at most 8 levels). */
 typedef struct {
   int status;            /* gpsoc_status of this solve */
   int iters;             /* iterations on the finest level */
@@ -114,6 +120,7 @@ typedef struct {
   int levels;
   int beta_resets, halvings, fp32_iters, fp64_iters;
   double energy, mu, mass[3], res_inf, dE_last;
+  int level_iters[8];
 } gpsoc_result;
 
 typedef struct gpsoc_problem gpsoc_problem;
@@ -211,6 +218,11 @@ gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, i
 gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, double* ms, int cap, int* n_kernels);
 const char* gpsoc_profile_name(const gpsoc_problem* p, int k);
 uint64_t gpsoc_kernel_launches(const gpsoc_problem* p);
+
+/* Arithmetic roofline probe (no counterpart in the paper): FP64 and FP32 FMA
+ * throughput of the current device in TFLOP/s (an FMA counts 2 flops), from
+ * independent FMA chains run for a few milliseconds.  Either pointer may be NULL. */
+gpsoc_status gpsoc_probe_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* Message describing the last failure on this thread ("" if none). */
 const char* gpsoc_last_error(void);

@@ -17,6 +17,7 @@
 // inverse (y is constant along an x row), the x D_y piece is carried as a
 // second array G = F_y^{-1}[v_y F_y A] and multiplied by x after the x inverse.
 #include "gpsoc_internal.cuh"
+#include "scalar.cuh"
 
 namespace gpsoc {
 
@@ -27,21 +28,42 @@ __device__ __forceinline__ void load_tw(cx_t<T>* s_tw, const cx_t<T>* tw, int n)
   for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) s_tw[k] = tw[k];
 }
 
-// spin terms shared by the pointwise epilogues:
+// spin terms shared by the pointwise epilogues (working precision W):
 //   a = conj(p0) p1 + conj(pm) p0  so that F_-/sqrt2 = a, F_+/sqrt2 = conj(a),
 //   F_x = sqrt2 Re a, F_y = -sqrt2 Im a, F_z = |p1|^2 - |pm|^2, |F|^2 = 2|a|^2 + F_z^2.
-template <class C>
-__device__ __forceinline__ double2 spin_a(C p1, C p0, C pm) {
-  double ar = (double)p0.x * p1.x + (double)p0.y * p1.y + (double)pm.x * p0.x + (double)pm.y * p0.y;
-  double ai = (double)p0.x * p1.y - (double)p0.y * p1.x + (double)pm.x * p0.y - (double)pm.y * p0.x;
-  return make_double2(ar, ai);
+template <class W, class C1, class C2, class C3>
+__device__ __forceinline__ void spin_a(C1 p1, C2 p0, C3 pm, W& ar, W& ai) {
+  ar = (W)p0.x * (W)p1.x + (W)p0.y * (W)p1.y + (W)pm.x * (W)p0.x + (W)pm.y * (W)p0.y;
+  ai = (W)p0.x * (W)p1.y - (W)p0.y * (W)p1.x + (W)pm.x * (W)p0.y - (W)pm.y * (W)p0.x;
+}
+
+template <class W> __device__ __forceinline__ W rsqrt_w(W x);
+template <> __device__ __forceinline__ double rsqrt_w<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_w<float>(float x) { return rsqrtf(x); }
+
+// write per-thread partial sums (working precision) as a deterministic FP64 block total
+template <int K, class W>
+__device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&slots)[K], const bool (&mx)[K],
+                                               double* red, double* part, long long sbase_slot, int pmax, int blk) {
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
+  block_reduce<K>(v, red, mx);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[(sbase_slot + slots[k]) * pmax + blk] = v[k];
+  }
 }
 
 // ============================================================== row passes (x axis)
+// Working precision W = T: FP64 kernels compute in double, FP32 kernels in float
+// (per-thread partial sums in T, block and grid reductions in FP64).
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   using C = cx_t<T>;
+  using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int last_flag;
   const int nx = A.g.n[0], Lx = A.g.log2n[0];
   const long long npts = A.g.npts;
   const int rows = (int)(npts / nx);
@@ -52,19 +74,25 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   C* s_tw = (C*)smem_raw;
   C* buf0 = s_tw + (nx >> 1);
   const int per = R * nx;             // elements of one component in the tile
+  constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
   C* buf1 = buf0 + 3 * per;
-  double* red = (double*)(buf1 + ((MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN) ? 3 * per : 0));
+  double* red = (double*)(buf1 + (two ? 3 * per : 0));
   load_tw<T>(s_tw, A.tw[0], nx);
   const long long sbase = (long long)s * 3 * npts;
   const long long rbase = (long long)rb * R * nx;   // offset of the tile inside a component
+  const long long sslot = (long long)s * NSLOT;
   const SolveState& S = A.st[s];
   const PhysDev ph = A.phys[s];
   const int ny = A.g.n[1];
 
-  if (MODE == ROW_FWD_PLAIN || MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE) {
-    double acc[1] = {0.0};
-    const double cproj = S.cproj, mu = A.given_r ? 0.0 : S.mu;
-    double al[3] = {S.alpha[0], S.alpha[1], S.alpha[2]};
+  if (MODE == ROW_FWD_PLAIN || MODE == ROW_FWD_UPD || MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE) {
+    W acc[1] = {(W)0};
+    const W cproj = (W)S.cproj, mu = A.given_r ? (W)0 : (W)S.mu, beta = (W)S.beta;
+    const bool use_prev = (MODE == ROW_FWD_PROJ) && S.beta != 0.0;
+    const bool upd = (MODE == ROW_FWD_UPD) && S.pending != 0;
+    const W uc = (W)S.upd_c, us = (W)S.upd_s, usc = (W)S.upd_scale;
+    const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
+    const W c0 = (W)ph.c0;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const long long off = rbase + e;
@@ -72,43 +100,59 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
       if (MODE == ROW_FWD_PLAIN) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) buf0[c * per + pos] = A.in0[sbase + c * npts + off];
-      } else if (MODE == ROW_FWD_PROJ) {
+      } else if (MODE == ROW_FWD_UPD) {
+        // the step accepted by the previous iteration: Phi <- (cos t Phi + sin t P/|P|)/norm
+        // (Eqs. formula-pcg, update); reduce max |dPhi|^2 for the stop1 test
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          C d = A.in0[sbase + c * npts + off];
-          C f = A.in1[sbase + c * npts + off];
+          C f = A.in0[sbase + c * npts + off];
+          if (upd) {
+            const C p = A.in2[sbase + c * npts + off];
+            const C o = mk<C>(usc * (uc * f.x + us * p.x), usc * (uc * f.y + us * p.y));
+            const W dr = o.x - f.x, di = o.y - f.y;
+            acc[0] = fmax(acc[0], dr * dr + di * di);
+            A.out1[sbase + c * npts + off] = o;
+            f = o;
+          }
+          buf0[c * per + pos] = f;
+        }
+      } else if (MODE == ROW_FWD_PROJ) {
+        // D = -z + beta P_prev, P = D - Re<D, Phi> Phi (Eq. formula-project); reduce ||P||^2
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const C z = A.in0[sbase + c * npts + off];
+          const C f = A.in1[sbase + c * npts + off];
+          W dr = -z.x, di = -z.y;
+          if (use_prev) { const C q = A.in2[sbase + c * npts + off]; dr += beta * q.x; di += beta * q.y; }
           C p;
-          p.x = (T)((double)d.x - cproj * (double)f.x);
-          p.y = (T)((double)d.y - cproj * (double)f.y);
+          p.x = dr - cproj * f.x;
+          p.y = di - cproj * f.y;
           A.out1[sbase + c * npts + off] = p;
-          acc[0] += (double)p.x * p.x + (double)p.y * p.y;
+          acc[0] += p.x * p.x + p.y * p.y;
           buf0[c * per + pos] = p;
         }
-      } else {  // ROW_FWD_PRE
+      } else {  // ROW_FWD_PRE: r = H Phi - mu Phi, then P_V^{1/2} r (Eq. PreCondPot)
         C f[3], h[3];
-        double rho = 0.0;
+        W rho = (W)0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           f[c] = A.in1[sbase + c * npts + off];
           h[c] = A.in0[sbase + c * npts + off];
-          rho += (double)f[c].x * f[c].x + (double)f[c].y * f[c].y;
+          rho += f[c].x * f[c].x + f[c].y * f[c].y;
         }
-        const long long gi = rbase + e;  // flat point index inside the component
-        const int ix = j;
-        const long long row = gi / nx;
-        const int iy = (int)(row % ny), iz = (int)(row / ny);
-        const double V = trap_value(A.trap, A.g, ix, iy, iz, gi);
+        const long long row = off / nx;
+        const W V = trap_value<W>(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          C r;
-          r.x = (T)((double)h[c].x - mu * (double)f[c].x);
-          r.y = (T)((double)h[c].y - mu * (double)f[c].y);
-          A.out1[sbase + c * npts + off] = r;
-          acc[0] = fmax(acc[0], sqrt((double)r.x * r.x + (double)r.y * r.y));
-          double den = al[c] + V + ph.c0 * rho;
-          den = fmax(den, 1e-12 * al[c]);
-          const double sc = 1.0 / sqrt(den);
-          buf0[c * per + pos] = mk<C>((double)r.x * sc, (double)r.y * sc);
+          C rr;
+          rr.x = h[c].x - mu * f[c].x;
+          rr.y = h[c].y - mu * f[c].y;
+          A.out1[sbase + c * npts + off] = rr;
+          acc[0] = fmax(acc[0], sqrt(rr.x * rr.x + rr.y * rr.y));
+          W den = al[c] + V + c0 * rho;
+          den = fmax(den, (W)1e-12 * al[c]);
+          const W sc = rsqrt_w<W>(den);
+          buf0[c * per + pos] = mk<C>(rr.x * sc, rr.y * sc);
         }
       }
     }
@@ -118,20 +162,17 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + rbase + e] = buf0[c * per + e];
     }
-    if (MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE) {
-      const bool mx[1] = {MODE == ROW_FWD_PRE};
-      block_reduce<1>(acc, (double*)buf0, mx);
-      if (threadIdx.x == 0) {
-        const int slot = (MODE == ROW_FWD_PROJ) ? SL_P2 : SL_RINF;
-        A.part[((long long)s * NSLOT + slot) * A.pmax + rb] = acc[0];
-      }
+    if (MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE || (MODE == ROW_FWD_UPD && upd)) {
+      const bool mx[1] = {MODE != ROW_FWD_PROJ};
+      const int slots[1] = {(MODE == ROW_FWD_PROJ) ? (int)SL_P2 : (MODE == ROW_FWD_PRE) ? (int)SL_RINF : (int)SL_DPHIINF};
+      store_partials<1, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
     }
+    if (MODE == ROW_FWD_PRE && A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_res(A.sc, s, red);
     return;
   }
 
   // ---------------------------------------------------------------- inverse passes
   // load natural order, DIF inverse -> bit-reversed positions in shared memory
-  const bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -142,84 +183,84 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   __syncthreads();
   fft_dif<C, false>(buf0, Lx, two ? 6 * R : 3 * R, two ? 6 * R : 3 * R, 0, nx, 1, s_tw, true);
 
-  const double inv_n = 1.0 / (double)npts;
-  const double Om = ph.Omega;
+  const W inv_n = (W)1 / (W)npts;
+  const W Om = (W)ph.Omega;
   if (MODE == ROW_INV_PLAIN) {
-    const double sc = A.scale;
+    const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const int pos = r * nx + bitrev(j, Lx);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C v = buf0[c * per + pos];
-        A.out0[sbase + c * npts + rbase + e] = mk<C>((double)v.x * sc, (double)v.y * sc);
+        const C v = buf0[c * per + pos];
+        A.out0[sbase + c * npts + rbase + e] = mk<C>(v.x * sc, v.y * sc);
       }
     }
     return;
   }
   if (MODE == ROW_INV_PRE) {
-    double acc[2] = {0.0, 0.0};
+    // z = P_V^{1/2} F^-1[...] (Eq. PreCondMix); reduce Re<r, z>, Re<r_prev, z>
+    W acc[2] = {(W)0, (W)0};
     const bool use_prev = (A.in3 != nullptr) && !S.first;
+    const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
+    const W c0 = (W)ph.c0;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const int pos = r * nx + bitrev(j, Lx);
       const long long off = rbase + e;
-      C f[3];
-      double rho = 0.0;
+      W rho = (W)0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        f[c] = A.in1[sbase + c * npts + off];
-        rho += (double)f[c].x * f[c].x + (double)f[c].y * f[c].y;
+        const C f = A.in1[sbase + c * npts + off];
+        rho += f.x * f.x + f.y * f.y;
       }
       const long long row = off / nx;
-      const double V = trap_value(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
+      const W V = trap_value<W>(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        double den = S.alpha[c] + V + ph.c0 * rho;
-        den = fmax(den, 1e-12 * S.alpha[c]);
-        const double sc = inv_n / sqrt(den);
-        C v = buf0[c * per + pos];
-        C z = mk<C>((double)v.x * sc, (double)v.y * sc);
+        W den = al[c] + V + c0 * rho;
+        den = fmax(den, (W)1e-12 * al[c]);
+        const W sc = inv_n * rsqrt_w<W>(den);
+        const C v = buf0[c * per + pos];
+        const C z = mk<C>(v.x * sc, v.y * sc);
         A.out0[sbase + c * npts + off] = z;
-        C rr = A.in2[sbase + c * npts + off];
-        acc[0] += (double)rr.x * z.x + (double)rr.y * z.y;
+        const C rr = A.in2[sbase + c * npts + off];
+        acc[0] += rr.x * z.x + rr.y * z.y;
         if (use_prev) {
-          C rp = A.in3[sbase + c * npts + off];
-          acc[1] += (double)rp.x * z.x + (double)rp.y * z.y;
+          const C rp = A.in3[sbase + c * npts + off];
+          acc[1] += rp.x * z.x + rp.y * z.y;
         }
       }
     }
     const bool mx[2] = {false, false};
-    block_reduce<2>(acc, red, mx);
-    if (threadIdx.x == 0) {
-      A.part[((long long)s * NSLOT + SL_RZ) * A.pmax + rb] = acc[0];
-      A.part[((long long)s * NSLOT + SL_RPZ) * A.pmax + rb] = acc[1];
-    }
+    const int slots[2] = {SL_RZ, SL_RPZ};
+    store_partials<2, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
+    if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_beta(A.sc, s, red);
     return;
   }
 
   // ROW_INV_H / ROW_INV_P / ROW_INV_LIN: lin = F_x^-1(T')/npts - Omega x F_x^-1(G)/npts + V u
-  const double c0 = ph.c0, c1 = ph.c1;
-  double acc[13];
+  const W c0 = (W)ph.c0, c1 = (W)ph.c1;
+  W acc[13];
 #pragma unroll
-  for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 13; ++k) acc[k] = (W)0;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int r = e / nx, j = e - r * nx;
     const int pos = r * nx + bitrev(j, Lx);
     const long long off = rbase + e;
     const long long row = off / nx;
     const int iy = (int)(row % ny), iz = (int)(row / ny);
-    const double x = -A.g.L[0] + j * A.g.h[0];
-    const double V = trap_value(A.trap, A.g, j, iy, iz, off);
+    const W x = (W)(-A.g.L[0]) + (W)j * (W)A.g.h[0];
+    const W V = trap_value<W>(A.trap, A.g, j, iy, iz, off);
     C u[3];  // Phi for ROW_INV_H, P for ROW_INV_P / ROW_INV_LIN
-    double lin_r[3], lin_i[3];
+    W lin_r[3], lin_i[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       u[c] = A.in2[sbase + c * npts + off];
-      C t = buf0[c * per + pos];
-      C gg = buf1[c * per + pos];
-      lin_r[c] = ((double)t.x - Om * x * (double)gg.x) * inv_n + V * (double)u[c].x;
-      lin_i[c] = ((double)t.y - Om * x * (double)gg.y) * inv_n + V * (double)u[c].y;
+      const C t = buf0[c * per + pos];
+      const C gg = buf1[c * per + pos];
+      lin_r[c] = (t.x - Om * x * gg.x) * inv_n + V * u[c].x;
+      lin_i[c] = (t.y - Om * x * gg.y) * inv_n + V * u[c].y;
     }
     if (MODE == ROW_INV_LIN) {
 #pragma unroll
@@ -228,26 +269,27 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
     }
     if (MODE == ROW_INV_H) {
       // nonlinear terms of Eqs. eigen1-eigen3: c0 rho phi + c1 (F.f) Phi
-      double m[3];
-      double rho = 0.0;
+      W m[3];
+      W rho = (W)0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) { m[c] = (double)u[c].x * u[c].x + (double)u[c].y * u[c].y; rho += m[c]; }
-      const double2 a = spin_a(u[0], u[1], u[2]);
-      const double Fz = m[0] - m[2];
+      for (int c = 0; c < 3; ++c) { m[c] = u[c].x * u[c].x + u[c].y * u[c].y; rho += m[c]; }
+      W ax, ay;
+      spin_a<W>(u[0], u[1], u[2], ax, ay);
+      const W Fz = m[0] - m[2];
       // (F.f)Phi: [Fz p1 + a p0, conj(a) p1 + a pm, conj(a) p0 - Fz pm]
-      double fr[3], fi[3];
-      fr[0] = Fz * u[0].x + (a.x * u[1].x - a.y * u[1].y);
-      fi[0] = Fz * u[0].y + (a.x * u[1].y + a.y * u[1].x);
-      fr[1] = (a.x * u[0].x + a.y * u[0].y) + (a.x * u[2].x - a.y * u[2].y);
-      fi[1] = (a.x * u[0].y - a.y * u[0].x) + (a.x * u[2].y + a.y * u[2].x);
-      fr[2] = (a.x * u[1].x + a.y * u[1].y) - Fz * u[2].x;
-      fi[2] = (a.x * u[1].y - a.y * u[1].x) - Fz * u[2].y;
-      double q = 0.0;
+      W fr[3], fi[3];
+      fr[0] = Fz * u[0].x + (ax * u[1].x - ay * u[1].y);
+      fi[0] = Fz * u[0].y + (ax * u[1].y + ay * u[1].x);
+      fr[1] = (ax * u[0].x + ay * u[0].y) + (ax * u[2].x - ay * u[2].y);
+      fi[1] = (ax * u[0].y - ay * u[0].x) + (ax * u[2].y + ay * u[2].x);
+      fr[2] = (ax * u[1].x + ay * u[1].y) - Fz * u[2].x;
+      fi[2] = (ax * u[1].y - ay * u[1].x) - Fz * u[2].y;
+      W q = (W)0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        q += (double)u[c].x * lin_r[c] + (double)u[c].y * lin_i[c];
-        const double hr = lin_r[c] + c0 * rho * u[c].x + c1 * fr[c];
-        const double hi = lin_i[c] + c0 * rho * u[c].y + c1 * fi[c];
+        q += u[c].x * lin_r[c] + u[c].y * lin_i[c];
+        const W hr = lin_r[c] + c0 * rho * u[c].x + c1 * fr[c];
+        const W hi = lin_i[c] + c0 * rho * u[c].y + c1 * fi[c];
         A.out0[sbase + c * npts + off] = mk<C>(hr, hi);
         acc[3 + c] += V * m[c];
         acc[6 + c] += rho * m[c];
@@ -255,41 +297,41 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
       }
       acc[0] += q;
       acc[1] += rho * rho;
-      acc[2] += 2.0 * (a.x * a.x + a.y * a.y) + Fz * Fz;
-    } else {  // ROW_INV_P: step-model reductions
+      acc[2] += (W)2 * (ax * ax + ay * ay) + Fz * Fz;
+    } else {  // ROW_INV_P: step-model reductions (Eqs. an, bn and the sin/cos form of E(theta))
       C f[3], h[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) { f[c] = A.in3[sbase + c * npts + off]; h[c] = A.in4[sbase + c * npts + off]; }
-      double hpp = 0.0, hphip = 0.0, R = 0.0, rf = 0.0, rp = 0.0;
+      W hpp = (W)0, hphip = (W)0, Rv = (W)0, rf = (W)0, rp = (W)0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         hpp += lin_r[c] * u[c].x + lin_i[c] * u[c].y;
-        hphip += (double)h[c].x * u[c].x + (double)h[c].y * u[c].y;
-        R += (double)f[c].x * u[c].x + (double)f[c].y * u[c].y;
-        rf += (double)f[c].x * f[c].x + (double)f[c].y * f[c].y;
-        rp += (double)u[c].x * u[c].x + (double)u[c].y * u[c].y;
+        hphip += h[c].x * u[c].x + h[c].y * u[c].y;
+        Rv += f[c].x * u[c].x + f[c].y * u[c].y;
+        rf += f[c].x * f[c].x + f[c].y * f[c].y;
+        rp += u[c].x * u[c].x + u[c].y * u[c].y;
       }
-      // spin vectors: F(Phi), F(P) and the symmetric cross term Re F~(Phi, P)
-      const double2 aF = spin_a(f[0], f[1], f[2]);
-      const double2 aP = spin_a(u[0], u[1], u[2]);
-      const double s2 = 1.4142135623730951;
-      const double FFx = s2 * aF.x, FFy = -s2 * aF.y;
-      const double FFz = ((double)f[0].x * f[0].x + (double)f[0].y * f[0].y) - ((double)f[2].x * f[2].x + (double)f[2].y * f[2].y);
-      const double FPx = s2 * aP.x, FPy = -s2 * aP.y;
-      const double FPz = ((double)u[0].x * u[0].x + (double)u[0].y * u[0].y) - ((double)u[2].x * u[2].x + (double)u[2].y * u[2].y);
-      // cross: Re(P^dag f_alpha Phi) = 1/2 d/de F_alpha(Phi + e P): a(Phi,P) + a(P,Phi) pieces
-      const double2 aX1 = spin_a(make_double2(f[0].x, f[0].y), make_double2(u[1].x, u[1].y), make_double2(f[2].x, f[2].y));
-      const double2 aX2 = spin_a(make_double2(u[0].x, u[0].y), make_double2(f[1].x, f[1].y), make_double2(u[2].x, u[2].y));
-      // a(Phi+eP) = a(Phi) + e (aX1 + aX2) + e^2 a(P): cross coefficient is (aX1 + aX2)
-      const double FXx = 0.5 * s2 * (aX1.x + aX2.x), FXy = -0.5 * s2 * (aX1.y + aX2.y);
-      const double FXz = ((double)f[0].x * u[0].x + (double)f[0].y * u[0].y) - ((double)f[2].x * u[2].x + (double)f[2].y * u[2].y);
+      // spin vectors F(Phi), F(P) and the symmetric cross term Re F~(Phi, P)
+      const W s2 = (W)1.4142135623730951;
+      W aFx, aFy, aPx, aPy, a1x, a1y, a2x, a2y;
+      spin_a<W>(f[0], f[1], f[2], aFx, aFy);
+      spin_a<W>(u[0], u[1], u[2], aPx, aPy);
+      // a(Phi + e P) = a(Phi) + e (a1 + a2) + e^2 a(P); Re F~ is half the e coefficient of F
+      spin_a<W>(f[0], u[1], f[2], a1x, a1y);
+      spin_a<W>(u[0], f[1], u[2], a2x, a2y);
+      const W FFx = s2 * aFx, FFy = -s2 * aFy;
+      const W FFz = (f[0].x * f[0].x + f[0].y * f[0].y) - (f[2].x * f[2].x + f[2].y * f[2].y);
+      const W FPx = s2 * aPx, FPy = -s2 * aPy;
+      const W FPz = (u[0].x * u[0].x + u[0].y * u[0].y) - (u[2].x * u[2].x + u[2].y * u[2].y);
+      const W FXx = (W)0.5 * s2 * (a1x + a2x), FXy = -(W)0.5 * s2 * (a1y + a2y);
+      const W FXz = (f[0].x * u[0].x + f[0].y * u[0].y) - (f[2].x * u[2].x + f[2].y * u[2].y);
       acc[0] += hpp;
       acc[1] += hphip;
-      acc[2] += R;
-      acc[3] += rf * R;
+      acc[2] += Rv;
+      acc[3] += rf * Rv;
       acc[4] += rf * rp;
-      acc[5] += R * R;
-      acc[6] += R * rp;
+      acc[5] += Rv * Rv;
+      acc[6] += Rv * rp;
       acc[7] += rp * rp;
       acc[8] += FFx * FXx + FFy * FXy + FFz * FXz;
       acc[9] += FFx * FPx + FFy * FPy + FFz * FPz;
@@ -299,18 +341,18 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
     }
   }
   if (MODE == ROW_INV_LIN) return;
-  const bool mx[13] = {false, false, false, false, false, false, false, false, false, false, false, false, false};
-  block_reduce<13>(acc, red, mx);
-  if (threadIdx.x == 0) {
-    double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
-    if (MODE == ROW_INV_H) {
-      const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
-      for (int k = 0; k < 12; ++k) P[(long long)slots[k] * A.pmax] = acc[k];
-    } else {
-      const int slots[13] = {SL_HPP, SL_HPHIP, SL_RPHI, SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,
-                             SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP};
-      for (int k = 0; k < 13; ++k) P[(long long)slots[k] * A.pmax] = acc[k];
-    }
+  const bool mx[13] = {};
+  if (MODE == ROW_INV_H) {
+    const W a12[12] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], acc[7], acc[8], acc[9], acc[10], acc[11]};
+    const bool mx12[12] = {};
+    const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
+    store_partials<12, W>(a12, slots, mx12, red, A.part, sslot, A.pmax, rb);
+    if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, red);
+  } else {
+    const int slots[13] = {SL_HPP, SL_HPHIP, SL_RPHI, SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,
+                           SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP};
+    store_partials<13, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
+    if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_step(A.sc, s, red);
   }
 }
 
@@ -320,6 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC) {
   using C = cx_t<T>;
+  using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int na = A.g.n[axis], La = A.g.log2n[axis];
   const long long npts = A.g.npts;
@@ -342,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const long long obase = (long long)o * na * ni + i0;
   const SolveState& S = A.st[s];
   const PhysDev ph = A.phys[s];
-  const double Lax = A.g.L[axis];
+  const double piA = A.g.piL[axis];
   const int nx = A.g.n[0];
 
   // load in0 tile: bit-reversed positions for forward (DIT) modes, natural for inverse (DIF)
@@ -374,24 +417,24 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   }
   if (MODE == COL_INV) {
     fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
-    const double sc = A.scale;
+    const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
       const int pj = bitrev(j, La);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C v = buf[c * per + pj * TC + t];
-        A.out0[sbase + c * npts + obase + (long long)j * ni + t] = mk<C>((double)v.x * sc, (double)v.y * sc);
+        const C v = buf[c * per + pj * TC + t];
+        A.out0[sbase + c * npts + obase + (long long)j * ni + t] = mk<C>(v.x * sc, v.y * sc);
       }
     }
     return;
   }
 
   // inner index -> (kx [, ky]) wavenumbers (inputs are spectral along the faster axes)
-  auto kinner = [&](int t, double& kx, double& ky) {
+  auto kinner = [&](int t, W& kx, W& ky) {
     const int ii = i0 + t;
-    if (axis == 1) { kx = wavenum(ii, nx, A.g.L[0]); ky = 0.0; }
-    else { kx = wavenum(ii % nx, nx, A.g.L[0]); ky = wavenum(ii / nx, A.g.n[1], A.g.L[1]); }
+    if (axis == 1) { kx = wavenum<W>(ii, nx, A.g.piL[0]); ky = (W)0; }
+    else { kx = wavenum<W>(ii % nx, nx, A.g.piL[0]); ky = wavenum<W>(ii / nx, A.g.n[1], A.g.piL[1]); }
   };
 
   if (MODE == COL_YINV_H) {
@@ -400,29 +443,29 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
     fft_dit<C, true>(buf2, La, 3 * TC, TC, per, 1, TC, s_tw, false);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
-      const int j = e / TC;
-      const double vy = wavenum(j, na, Lax);
+      const W vy = wavenum<W>(e / TC, na, piA);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf2[c * per + e] = cscale(buf2[c * per + e], (T)vy);
+      for (int c = 0; c < 3; ++c) buf2[c * per + e] = cscale(buf2[c * per + e], vy);
     }
     __syncthreads();
     fft_dif<C, true>(buf2, La, 3 * TC, TC, per, 1, TC, s_tw, true);
-    const double nfac = (double)A.g.n[1] * A.g.n[2];  // ny * nz
+    const W nfac = (W)A.g.n[1] * (W)A.g.n[2];  // ny * nz
+    const W nz = (W)A.g.n[2];
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
       const int pj = bitrev(j, La);
-      double kx, ky;
+      W kx, ky;
       kinner(t, kx, ky);
-      const double y = -A.g.L[1] + j * A.g.h[1];
-      const double rot = nfac * ph.Omega * y * kx;
+      const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
+      const W rot = nfac * (W)ph.Omega * y * kx;
       const long long gi = sbase + obase + (long long)j * ni + t;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C a = A.in1[gi + c * npts];
-        C cv = buf[c * per + pj * TC + t];
-        A.out0[gi + c * npts] = mk<C>((double)cv.x + rot * a.x, (double)cv.y + rot * a.y);
-        C gv = buf2[c * per + pj * TC + t];
-        A.out1[gi + c * npts] = mk<C>((double)gv.x * A.g.n[2], (double)gv.y * A.g.n[2]);
+        const C a = A.in1[gi + c * npts];
+        const C cv = buf[c * per + pj * TC + t];
+        A.out0[gi + c * npts] = mk<C>(cv.x + rot * a.x, cv.y + rot * a.y);
+        const C gv = buf2[c * per + pj * TC + t];
+        A.out1[gi + c * npts] = mk<C>(gv.x * nz, gv.y * nz);
       }
     }
     return;
@@ -434,10 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   if (MODE == COL_YMID_H) {
     // G_c = F_y^-1[v_y F_y A_c], one component at a time through buf2 (1 component)
     for (int c = 0; c < 3; ++c) {
-      for (int e = threadIdx.x; e < per; e += blockDim.x) {
-        const int j = e / TC;
-        buf2[e] = cscale(buf[c * per + e], (T)wavenum(j, na, Lax));
-      }
+      for (int e = threadIdx.x; e < per; e += blockDim.x) buf2[e] = cscale(buf[c * per + e], wavenum<W>(e / TC, na, piA));
       __syncthreads();
       fft_dif<C, true>(buf2, La, TC, TC, 0, 1, TC, s_tw, true);
       for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -448,60 +488,57 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     }
   }
 
-  double acc[3] = {0.0, 0.0, 0.0};
+  W acc[3] = {(W)0, (W)0, (W)0};
   // pointwise in k: the kinetic + SOC symbol (H chains) or the kinetic preconditioner
+  const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
+  const W g = (W)ph.gamma;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    double kx, ky, kz = 0.0;
+    W kx, ky, kz = (W)0;
     kinner(t, kx, ky);
-    if (axis == 1) ky = wavenum(j, na, Lax);
-    else kz = wavenum(j, na, Lax);
-    const double k2h = 0.5 * (kx * kx + ky * ky + kz * kz);
+    if (axis == 1) ky = wavenum<W>(j, na, piA);
+    else kz = wavenum<W>(j, na, piA);
+    const W k2h = (W)0.5 * (kx * kx + ky * ky + kz * kz);
     if (MODE == COL_MID_PRE) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf[c * per + e] = cscale(buf[c * per + e], (T)(1.0 / (S.alpha[c] + k2h)));
+      for (int c = 0; c < 3; ++c) buf[c * per + e] = cscale(buf[c * per + e], (W)1 / (al[c] + k2h));
     } else {
-      C p1 = buf[e], p0 = buf[per + e], pm = buf[2 * per + e];
+      const C p1 = buf[e], p0 = buf[per + e], pm = buf[2 * per + e];
       // kinetic per component (Parseval): sum 1/2 |k|^2 |phat_l|^2
-      acc[0] += k2h * ((double)p1.x * p1.x + (double)p1.y * p1.y);
-      acc[1] += k2h * ((double)p0.x * p0.x + (double)p0.y * p0.y);
-      acc[2] += k2h * ((double)pm.x * pm.x + (double)pm.y * pm.y);
+      acc[0] += k2h * (p1.x * p1.x + p1.y * p1.y);
+      acc[1] += k2h * (p0.x * p0.x + p0.y * p0.y);
+      acc[2] += k2h * (pm.x * pm.x + pm.y * pm.y);
       // -gamma S symbol: s0 = -kx + i ky (L0), s1 = -(kx + i ky) (L1)
       // out_1 = K p1 - g s0 p0 ; out_0 = K p0 - g (s1 p1 + s0 pm) ; out_-1 = K pm - g s1 p0
-      const double g = ph.gamma;
-      const double s0r = -kx, s0i = ky, s1r = -kx, s1i = -ky;
-      auto mul = [](double ar, double ai, C b, double& rr, double& ri) {
-        rr = ar * b.x - ai * b.y; ri = ar * b.y + ai * b.x;
-      };
-      double ar, ai, br, bi;
-      mul(s0r, s0i, p0, ar, ai);
-      const C o1 = mk<C>(k2h * p1.x - g * ar, k2h * p1.y - g * ai);
-      mul(s1r, s1i, p1, ar, ai);
-      mul(s0r, s0i, pm, br, bi);
-      const C o0 = mk<C>(k2h * p0.x - g * (ar + br), k2h * p0.y - g * (ai + bi));
-      mul(s1r, s1i, p0, ar, ai);
-      const C om = mk<C>(k2h * pm.x - g * ar, k2h * pm.y - g * ai);
-      buf[e] = o1; buf[per + e] = o0; buf[2 * per + e] = om;
+      const W s0r = -kx, s0i = ky, s1r = -kx, s1i = -ky;
+      const W a_r = s0r * p0.x - s0i * p0.y, a_i = s0r * p0.y + s0i * p0.x;   // s0 p0
+      const W b_r = s1r * p1.x - s1i * p1.y, b_i = s1r * p1.y + s1i * p1.x;   // s1 p1
+      const W c_r = s0r * pm.x - s0i * pm.y, c_i = s0r * pm.y + s0i * pm.x;   // s0 pm
+      const W d_r = s1r * p0.x - s1i * p0.y, d_i = s1r * p0.y + s1i * p0.x;   // s1 p0
+      buf[e] = mk<C>(k2h * p1.x - g * a_r, k2h * p1.y - g * a_i);
+      buf[per + e] = mk<C>(k2h * p0.x - g * (b_r + c_r), k2h * p0.y - g * (b_i + c_i));
+      buf[2 * per + e] = mk<C>(k2h * pm.x - g * d_r, k2h * pm.y - g * d_i);
     }
   }
   __syncthreads();
   fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
 
-  const double nrot = (double)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
+  const W nrot = (W)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
+  const W Om = (W)ph.Omega;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
     const int pj = bitrev(j, La);
     const long long gi = sbase + obase + (long long)j * ni + t;
     if (MODE == COL_YMID_H) {
-      double kx, ky;
+      W kx, ky;
       kinner(t, kx, ky);
-      const double y = -A.g.L[1] + j * A.g.h[1];
-      const double rot = nrot * ph.Omega * y * kx;
+      const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
+      const W rot = nrot * Om * y * kx;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        C a = A.in0[gi + c * npts];
-        C v = buf[c * per + pj * TC + t];
-        A.out0[gi + c * npts] = mk<C>((double)v.x + rot * a.x, (double)v.y + rot * a.y);
+        const C a = A.in0[gi + c * npts];
+        const C v = buf[c * per + pj * TC + t];
+        A.out0[gi + c * npts] = mk<C>(v.x + rot * a.x, v.y + rot * a.y);
       }
     } else {
 #pragma unroll
@@ -510,23 +547,22 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   }
   if (MODE == COL_MID_H || MODE == COL_YMID_H) {
     const bool mx[3] = {false, false, false};
-    block_reduce<3>(acc, red, mx);
-    if (threadIdx.x == 0) {
-      double* P = A.part + (long long)s * NSLOT * A.pmax + tb;
-      P[(long long)SL_KIN0 * A.pmax] = acc[0];
-      P[(long long)SL_KIN1 * A.pmax] = acc[1];
-      P[(long long)SL_KIN2 * A.pmax] = acc[2];
-    }
+    const int slots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
+    store_partials<3, W>(acc, slots, mx, red, A.part, (long long)s * NSLOT, A.pmax, tb);
   }
 }
 
 // ============================================================== launch helpers
+// Tile shapes depend on the grid only (never on the batch), so a solve reduces
+// in the same order alone and inside a batch.  Small grids get small tiles so
+// that one solve still spreads over many SMs.
 template <class T>
 int row_rows_per_block(const Geo& g) {
   const int nx = g.n[0];
   const int rows = (int)(g.npts / nx);
   int R = 512 / nx;
   if (R < 1) R = 1;
+  while (R > 1 && rows / R < 256) R >>= 1;
   if (R > rows) R = rows;
   return R;
 }
@@ -535,11 +571,21 @@ template <class T>
 int col_tc(const Geo& g, int axis) {
   const int na = g.n[axis];
   const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
-  const int target = (sizeof(T) == 8) ? 1024 : 2048;   // elements of one component per tile
+  const int no = (int)(g.npts / ((long long)na * ni));
+  const int tmin = (sizeof(T) == 8) ? 2 : 4;            // >= one 32-byte sector per line segment
+  const int target = (sizeof(T) == 8) ? 1024 : 2048;    // elements of one component per tile
   int tc = target / na;
   if (tc < 1) tc = 1;
+  while (tc > tmin && (ni / tc) * no < 256) tc >>= 1;
   if (tc > ni) tc = ni;
   return tc;
+}
+
+static int threads_for(int per) {
+  int t = (3 * per) / 2;   // butterflies per stage of the three components
+  if (t > 256) t = 256;
+  if (t < 64) t = 64;
+  return (t + 31) & ~31;
 }
 
 template <class T>
@@ -561,14 +607,14 @@ static size_t row_smem(const Geo& g, int mode) {
   const int R = row_rows_per_block<T>(g);
   const int per = R * g.n[0];
   const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
-  return sizeof(C) * ((g.n[0] >> 1) + 3 * per * (two ? 2 : 1)) + 32 * 13 * sizeof(double);
+  return sizeof(C) * ((g.n[0] >> 1) + 3 * per * (two ? 2 : 1)) + 160 * sizeof(double);
 }
 
 template <class T>
 static size_t col_smem(const Geo& g, int axis) {
   using C = cx_t<T>;
   const int per = g.n[axis] * col_tc<T>(g, axis);
-  return sizeof(C) * ((g.n[axis] >> 1) + 6 * per) + 32 * 3 * sizeof(double);
+  return sizeof(C) * ((g.n[axis] >> 1) + 6 * per) + 160 * sizeof(double);
 }
 
 template <class T, int MODE>
@@ -576,7 +622,7 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int R = row_rows_per_block<T>(a.g);
   const int nb = row_blocks_per_solve<T>(a.g, Launch{}) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE);
-  k_row<T, MODE><<<nb, kThreads, sm, st>>>(a, R);
+  k_row<T, MODE><<<nb, threads_for(R * a.g.n[0]), sm, st>>>(a, R);
 }
 
 template <class T>
@@ -590,6 +636,7 @@ void launch_row(int mode, const ChainArgs<T>& a, int, const Launch&, cudaStream_
     case ROW_INV_PRE: row_go<T, ROW_INV_PRE>(a, st); break;
     case ROW_INV_PLAIN: row_go<T, ROW_INV_PLAIN>(a, st); break;
     case ROW_INV_LIN: row_go<T, ROW_INV_LIN>(a, st); break;
+    case ROW_FWD_UPD: row_go<T, ROW_FWD_UPD>(a, st); break;
   }
 }
 
@@ -598,7 +645,7 @@ static void col_go(int axis, const ChainArgs<T>& a, cudaStream_t st) {
   const int tc = col_tc<T>(a.g, axis);
   const int nb = col_blocks_per_solve<T>(a.g, axis, Launch{}) * a.nsolve;
   const size_t sm = col_smem<T>(a.g, axis);
-  k_col<T, MODE><<<nb, kThreads, sm, st>>>(a, axis, tc);
+  k_col<T, MODE><<<nb, threads_for(tc * a.g.n[axis]), sm, st>>>(a, axis, tc);
 }
 
 template <class T>
@@ -621,7 +668,7 @@ cudaError_t chain_prepare() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   GPSOC_ATTR((k_row<T, ROW_FWD_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_FWD_PROJ>)) GPSOC_ATTR((k_row<T, ROW_FWD_PRE>))
   GPSOC_ATTR((k_row<T, ROW_INV_H>)) GPSOC_ATTR((k_row<T, ROW_INV_P>)) GPSOC_ATTR((k_row<T, ROW_INV_PRE>))
-  GPSOC_ATTR((k_row<T, ROW_INV_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_INV_LIN>))
+  GPSOC_ATTR((k_row<T, ROW_INV_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_INV_LIN>)) GPSOC_ATTR((k_row<T, ROW_FWD_UPD>))
   GPSOC_ATTR((k_col<T, COL_FWD>)) GPSOC_ATTR((k_col<T, COL_INV>)) GPSOC_ATTR((k_col<T, COL_MID_H>))
   GPSOC_ATTR((k_col<T, COL_MID_PRE>)) GPSOC_ATTR((k_col<T, COL_YMID_H>)) GPSOC_ATTR((k_col<T, COL_YINV_H>))
 #undef GPSOC_ATTR

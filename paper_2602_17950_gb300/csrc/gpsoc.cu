@@ -72,22 +72,22 @@ struct Bufs {
 
 const char* row_name(int m) {
   static const char* n[] = {"row_fwd", "row_fwd_proj", "row_fwd_pre", "row_inv_h", "row_inv_p", "row_inv_pre",
-                            "row_inv_plain", "row_inv_lin"};
-  return n[m];
+                            "row_inv_plain", "row_inv_lin", "row_fwd_upd"};
+  return (m >= 0 && m < (int)(sizeof(n) / sizeof(n[0]))) ? n[m] : "row_?";
 }
 const char* col_name(int m, int axis) {
   static const char* n[2][7] = {{"coly_fwd", "coly_inv", "coly_mid_h", "coly_mid_pre", "coly_ymid_h", "coly_yinv_h", "coly_kin"},
                                 {"colz_fwd", "colz_inv", "colz_mid_h", "colz_mid_pre", "colz_ymid_h", "colz_yinv_h", "colz_kin"}};
-  return n[axis == 2 ? 1 : 0][m];
+  return (m >= 0 && m < 7) ? n[axis == 2 ? 1 : 0][m] : "col_?";
 }
 const char* scalar_name(int ph) {
-  static const char* n[] = {"sc_init", "sc_obs", "sc_res", "sc_beta", "sc_cproj", "sc_step", "sc_cproj_reset",
-                            "sc_step_reset", "sc_norm", "sc_model"};
-  return n[ph];
+  static const char* n[] = {"sc_init", "sc_obs", "sc_res", "sc_beta", "sc_cproj", "sc_step", "sc_clear",
+                            "sc_norm", "sc_model"};
+  return (ph >= 0 && ph < (int)(sizeof(n) / sizeof(n[0]))) ? n[ph] : "sc_?";
 }
 const char* elem_name(int m) {
   static const char* n[] = {"el_dir", "el_update", "el_mass", "el_scale"};
-  return n[m];
+  return (m >= 0 && m < (int)(sizeof(n) / sizeof(n[0]))) ? n[m] : "el_?";
 }
 }  // namespace
 
@@ -106,22 +106,26 @@ struct gpsoc_problem {
   SolveState* h_st = nullptr;   // pinned mirror
   double* d_part = nullptr;
   int pmax = 0;
+  unsigned* d_cnt = nullptr;    // per-solve block arrival counters of the fused scalar steps
   double* d_scale = nullptr;    // per-solve scale factors
   double* d_tmp = nullptr;      // 3*batch doubles + model outputs
   size_t tmp_len = 0;
   Bufs<double> b64;
+  Bufs<float> b32;              // FP32 working set of mixed-precision solves (allocated on first use)
   std::map<int, double2*> tw64;
+  std::map<int, float2*> tw32;
   int level = 0;
   bool has_state = false;
   int max_level = 0;
   // captured iteration graph (two iterations) for the current level / options
-  cudaGraphExec_t graph = nullptr;
-  int graph_level = -1;
-  OptsDev graph_opts{};
-  uint64_t graph_kernels = 0;   // kernels per replay of the captured graph
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0] FP64, [1] FP32 iteration graphs
+  int graph_level[2] = {-1, -1};
+  OptsDev graph_opts[2]{};
+  uint64_t graph_kernels[2] = {0, 0};   // kernels per replay of the captured graph
   uint64_t launches = 0;        // kernels launched so far (graph replays included)
   Tracker* tr = nullptr;        // active tracker while enqueueing
   std::vector<std::string> prof_names;
+  std::vector<std::vector<int>> level_iters;   // per solve, iterations per level of the last solve
 };
 
 namespace {
@@ -141,7 +145,7 @@ void CL(gpsoc_problem* p, int mode, int axis, const ChainArgs<T>& a) {
   mark(p, col_name(mode, axis));
 }
 void SL(gpsoc_problem* p, const ScalarArgs& x) {
-  SL(p, x);
+  launch_scalar(x, p->stream);
   mark(p, scalar_name(x.phase));
 }
 template <class T>
@@ -160,11 +164,13 @@ Geo make_geo(const gpsoc_problem* p, int level) {
       g.n[i] = p->n[i] >> level;
       g.L[i] = p->L[i];
       g.h[i] = 2.0 * p->L[i] / g.n[i];
+      g.piL[i] = 3.14159265358979323846 / p->L[i];
       g.dV *= g.h[i];
     } else {
       g.n[i] = 1;
       g.L[i] = 1.0;
       g.h[i] = 1.0;
+      g.piL[i] = 0.0;
     }
     g.log2n[i] = ilog2(g.n[i]);
     g.npts *= g.n[i];
@@ -198,6 +204,28 @@ gpsoc_status twiddles(gpsoc_problem* p, int n, const double2** out) {
   return GPSOC_OK;
 }
 
+gpsoc_status twiddles(gpsoc_problem* p, int n, const float2** out) {
+  auto it = p->tw32.find(n);
+  if (it != p->tw32.end()) { *out = it->second; return GPSOC_OK; }
+  const double2* d64;
+  gpsoc_status s = twiddles(p, n, &d64);
+  if (s != GPSOC_OK) return s;
+  std::vector<double2> h(n / 2);
+  CK(cudaMemcpy(h.data(), d64, sizeof(double2) * (n / 2), cudaMemcpyDeviceToHost));
+  std::vector<float2> f(n / 2);
+  for (int k = 0; k < n / 2; ++k) f[k] = make_float2((float)h[k].x, (float)h[k].y);
+  float2* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(float2) * (n / 2 > 0 ? n / 2 : 1)));
+  CK(cudaMemcpy(d, f.data(), sizeof(float2) * (n / 2), cudaMemcpyHostToDevice));
+  p->tw32[n] = d;
+  *out = d;
+  return GPSOC_OK;
+}
+
+template <class T> Bufs<T>& bufs(gpsoc_problem* p);
+template <> Bufs<double>& bufs<double>(gpsoc_problem* p) { return p->b64; }
+template <> Bufs<float>& bufs<float>(gpsoc_problem* p) { return p->b32; }
+
 template <class T>
 gpsoc_status chain_args(gpsoc_problem* p, int level, ChainArgs<T>& a) {
   a = ChainArgs<T>{};
@@ -210,9 +238,10 @@ gpsoc_status chain_args(gpsoc_problem* p, int level, ChainArgs<T>& a) {
   a.nsolve = p->batch;
   a.gate = GATE_ACTIVE;
   a.scale = 1.0;
+  a.cnt = p->d_cnt;
   for (int i = 0; i < 3; ++i) {
     if (i < p->dim) {
-      const double2* tw;
+      const cx_t<T>* tw;
       gpsoc_status s = twiddles(p, a.g.n[i], &tw);
       if (s != GPSOC_OK) return s;
       a.tw[i] = tw;
@@ -221,6 +250,7 @@ gpsoc_status chain_args(gpsoc_problem* p, int level, ChainArgs<T>& a) {
   return GPSOC_OK;
 }
 
+template <class T = double>
 ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   ScalarArgs s{};
   s.st = p->d_st;
@@ -228,8 +258,8 @@ ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   s.part = p->d_part;
   s.pmax = p->pmax;
   Launch lc{};
-  s.nb_row = row_blocks_per_solve<double>(g, lc);
-  s.nb_col = col_blocks_per_solve<double>(g, p->dim - 1, lc);
+  s.nb_row = row_blocks_per_solve<T>(g, lc);
+  s.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, lc);
   s.nsolve = p->batch;
   s.phase = phase;
   s.npts = g.npts;
@@ -237,6 +267,22 @@ ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   s.norm_scale = p->d_scale;
   (void)level;
   return s;
+}
+
+template <class T>
+ScalarCtx scalar_ctx(gpsoc_problem* p, const Geo& g, const OptsDev& o, int flags) {
+  ScalarCtx c{};
+  c.st = p->d_st;
+  c.phys = p->d_phys;
+  c.part = p->d_part;
+  c.pmax = p->pmax;
+  c.nb_row = row_blocks_per_solve<T>(g, Launch{});
+  c.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, Launch{});
+  c.npts = g.npts;
+  c.dV = g.dV;
+  c.opts = o;
+  c.flags = flags;
+  return c;
 }
 
 template <class T>
@@ -253,60 +299,10 @@ ElemArgs<T> elem_args(gpsoc_problem* p, const Geo& g, int gate) {
   return e;
 }
 
-// H(Phi) chain: src -> dst (H(src) with nonlinear terms) and energy reductions
+// Spectral middle of the H chain: A = F_x(u) -> (T', G) (2D: one y pass; 3D: y fwd, z symbol, y inverse)
 template <class T>
-void run_h_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* src, cx_t<T>* dst) {
-  cudaStream_t st = p->stream;
-  Launch lc{};
-  a.in0 = src; a.out0 = B.A;
-  RL<T>(p, ROW_FWD_PLAIN, a);
-  if (p->dim == 2) {
-    a.in0 = B.A; a.out0 = B.W; a.out1 = B.G;
-    CL<T>(p, COL_YMID_H, 1, a);
-  } else {
-    a.in0 = B.A; a.out0 = B.B;
-    CL<T>(p, COL_FWD, 1, a);
-    a.in0 = B.B; a.out0 = B.B;
-    CL<T>(p, COL_MID_H, 2, a);
-    a.in0 = B.B; a.in1 = B.A; a.out0 = B.W; a.out1 = B.G;
-    CL<T>(p, COL_YINV_H, 1, a);
-  }
-  a.in0 = B.W; a.in1 = B.G; a.in2 = src; a.out0 = dst; a.out1 = nullptr;
-  RL<T>(p, ROW_INV_H, a);
-}
-
-// preconditioner chain: r = in0 - mu Phi (or in0 given as r) -> rout, z = P_C r -> zout
-template <class T>
-void run_pre_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* hphi, const cx_t<T>* phi,
-                   cx_t<T>* rout, const cx_t<T>* rprev, cx_t<T>* zout, bool res_phase, const ScalarArgs* sres) {
-  cudaStream_t st = p->stream;
-  Launch lc{};
-  a.in0 = hphi; a.in1 = phi; a.out0 = B.A; a.out1 = rout;
-  RL<T>(p, ROW_FWD_PRE, a);
-  if (res_phase && sres) SL(p, *sres);
-  a.given_r = 0;
-  if (p->dim == 2) {
-    a.in0 = B.A; a.out0 = B.A;
-    CL<T>(p, COL_MID_PRE, 1, a);
-  } else {
-    a.in0 = B.A; a.out0 = B.A;
-    CL<T>(p, COL_FWD, 1, a);
-    CL<T>(p, COL_MID_PRE, 2, a);
-    a.scale = 1.0;
-    CL<T>(p, COL_INV, 1, a);
-  }
-  a.in0 = B.A; a.in1 = phi; a.in2 = rout; a.in3 = rprev; a.out0 = zout;
-  RL<T>(p, ROW_INV_PRE, a);
-}
-
-// P chain: P = D - cproj Phi -> pout, step-model reductions
-template <class T>
-void run_p_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* D, const cx_t<T>* phi,
-                 const cx_t<T>* hphi, cx_t<T>* pout) {
-  cudaStream_t st = p->stream;
-  Launch lc{};
-  a.in0 = D; a.in1 = phi; a.out0 = B.A; a.out1 = pout;
-  RL<T>(p, ROW_FWD_PROJ, a);
+void h_middle(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B) {
+  a.fuse = 0;
   if (p->dim == 2) {
     a.in0 = B.A; a.out0 = B.W; a.out1 = B.G;
     CL<T>(p, COL_YMID_H, 1, a);
@@ -318,48 +314,110 @@ void run_p_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* D,
     a.in0 = B.B; a.in1 = B.A; a.out0 = B.W; a.out1 = B.G;
     CL<T>(p, COL_YINV_H, 1, a);
   }
-  a.in0 = B.W; a.in1 = B.G; a.in2 = pout; a.in3 = phi; a.in4 = hphi; a.out0 = nullptr; a.out1 = nullptr;
-  RL<T>(p, ROW_INV_P, a);
 }
 
-// One PCG iteration for all active solves (Algorithm 1 with Algorithm 2).
+// H(Phi) chain: src -> dst (H(src) with nonlinear terms) and energy reductions.
+// With pending_P != nullptr the first pass applies the pending accepted step.
+template <class T>
+void run_h_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, cx_t<T>* src, cx_t<T>* dst,
+                 const cx_t<T>* pending_P = nullptr, int fuse_obs = 0) {
+  ChainArgs<T> f = a;
+  f.fuse = 0;
+  if (pending_P) {
+    f.in0 = src; f.in2 = pending_P; f.out1 = src; f.out0 = B.A;
+    RL<T>(p, ROW_FWD_UPD, f);
+  } else {
+    f.in0 = src; f.out0 = B.A;
+    RL<T>(p, ROW_FWD_PLAIN, f);
+  }
+  h_middle<T>(p, a, B);
+  ChainArgs<T> g = a;
+  g.fuse = fuse_obs;
+  g.in0 = B.W; g.in1 = B.G; g.in2 = src; g.out0 = dst; g.out1 = nullptr;
+  RL<T>(p, ROW_INV_H, g);
+}
+
+// preconditioner chain: r = in0 - mu Phi (or in0 given as r) -> rout, z = P_C r -> zout
+template <class T>
+void run_pre_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* hphi, const cx_t<T>* phi,
+                   cx_t<T>* rout, const cx_t<T>* rprev, cx_t<T>* zout, int fuse) {
+  ChainArgs<T> f = a;
+  f.fuse = fuse;
+  f.in0 = hphi; f.in1 = phi; f.out0 = B.A; f.out1 = rout;
+  RL<T>(p, ROW_FWD_PRE, f);
+  ChainArgs<T> m = a;
+  m.fuse = 0;
+  m.given_r = 0;
+  if (p->dim == 2) {
+    m.in0 = B.A; m.out0 = B.A;
+    CL<T>(p, COL_MID_PRE, 1, m);
+  } else {
+    m.in0 = B.A; m.out0 = B.A;
+    CL<T>(p, COL_FWD, 1, m);
+    CL<T>(p, COL_MID_PRE, 2, m);
+    m.scale = 1.0;
+    CL<T>(p, COL_INV, 1, m);
+  }
+  ChainArgs<T> iv = a;
+  iv.fuse = fuse;
+  iv.given_r = 0;
+  iv.in0 = B.A; iv.in1 = phi; iv.in2 = rout; iv.in3 = rprev; iv.out0 = zout;
+  RL<T>(p, ROW_INV_PRE, iv);
+}
+
+// P chain: P = -z + beta P_prev - cproj Phi -> pout, step-model reductions
+template <class T>
+void run_p_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* z, const cx_t<T>* pprev,
+                 const cx_t<T>* phi, const cx_t<T>* hphi, cx_t<T>* pout, int fuse_step) {
+  ChainArgs<T> f = a;
+  f.fuse = 0;
+  f.in0 = z; f.in1 = phi; f.in2 = pprev; f.out0 = B.A; f.out1 = pout;
+  RL<T>(p, ROW_FWD_PROJ, f);
+  h_middle<T>(p, a, B);
+  ChainArgs<T> g = a;
+  g.fuse = fuse_step;
+  g.in0 = B.W; g.in1 = B.G; g.in2 = pout; g.in3 = phi; g.in4 = hphi; g.out0 = nullptr; g.out1 = nullptr;
+  RL<T>(p, ROW_INV_P, g);
+}
+
+// One PCG iteration for all active solves (Algorithm 1 with Algorithm 2), ten
+// kernels; every scalar step runs in the last block of the pass that produces
+// its sums.  The step accepted here is applied by the first pass of the next
+// iteration (or by flush_pending).
 template <class T>
 gpsoc_status enqueue_iteration(gpsoc_problem* p, int level, Bufs<T>& B, int parity, const OptsDev& o, int fp32) {
-  cudaStream_t st = p->stream;
   ChainArgs<T> a;
   gpsoc_status s = chain_args<T>(p, level, a);
   if (s != GPSOC_OK) return s;
   const Geo g = a.g;
-  auto sc = [&](int phase) {
-    ScalarArgs x = scalar_args(p, level, phase, g);
-    x.opts = o;
-    x.flags = fp32 ? 2 : 0;
-    SL(p, x);
-  };
+  a.sc = scalar_ctx<T>(p, g, o, fp32 ? 2 : 0);
   const int cur = parity & 1, prv = cur ^ 1;
-  // H(Phi^n), E, mu, alpha
-  run_h_chain<T>(p, a, B, B.Phi, B.HPhi);
-  sc(PH_OBS);
-  // r^n, stopping test, P_C r^n
-  ScalarArgs sres = scalar_args(p, level, PH_RES, g);
-  sres.opts = o;
-  run_pre_chain<T>(p, a, B, B.HPhi, B.Phi, B.R[cur], B.R[prv], B.Z, true, &sres);
-  sc(PH_BETA);
-  // D^n, P^n, step model, Algorithm 2
-  for (int round = 0; round < 2; ++round) {
-    ElemArgs<T> e = elem_args<T>(p, g, round == 0 ? GATE_ACTIVE : GATE_RESET);
-    e.in0 = B.Z; e.in1 = B.P[prv]; e.in2 = B.Phi; e.out0 = B.D;
-    EL<T>(p, EL_DIR, e);
-    sc(round == 0 ? PH_CPROJ : PH_CPROJ_RESET);
-    ChainArgs<T> ap = a;
-    ap.gate = (round == 0) ? GATE_ACTIVE : GATE_RESET;
-    run_p_chain<T>(p, ap, B, B.D, B.Phi, B.HPhi, B.P[cur]);
-    sc(round == 0 ? PH_STEP : PH_STEP_RESET);
-  }
-  // Phi^{n+1}
+  // apply the pending step, H(Phi^n), E, mu, alpha
+  run_h_chain<T>(p, a, B, B.Phi, B.HPhi, B.P[prv], 1);
+  // r^n, stopping test, P_C r^n, beta
+  run_pre_chain<T>(p, a, B, B.HPhi, B.Phi, B.R[cur], B.R[prv], B.Z, 1);
+  // Re<D, Phi> and the beta = 0 decision
   ElemArgs<T> e = elem_args<T>(p, g, GATE_ACTIVE);
-  e.in0 = B.P[cur]; e.out0 = B.Phi;
+  e.in0 = B.Z; e.in1 = B.P[prv]; e.in2 = B.Phi; e.in3 = B.HPhi;
+  e.fuse = 1;
+  e.cnt = p->d_cnt;
+  e.sc = a.sc;
+  EL<T>(p, EL_DIR, e);
+  // P^n, step model, Algorithm 2
+  run_p_chain<T>(p, a, B, B.Z, B.P[prv], B.Phi, B.HPhi, B.P[cur], 1);
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+// apply steps accepted by the last enqueued iteration (parity of that iteration given)
+template <class T>
+gpsoc_status flush_pending(gpsoc_problem* p, int level, Bufs<T>& B, int last_parity) {
+  const Geo g = make_geo(p, level);
+  ElemArgs<T> e = elem_args<T>(p, g, GATE_PENDING);
+  e.in0 = B.P[last_parity & 1]; e.out0 = B.Phi;
   EL<T>(p, EL_UPDATE, e);
+  ScalarArgs x = scalar_args<T>(p, level, PH_CLEAR, g);
+  SL(p, x);
   CK(cudaGetLastError());
   return GPSOC_OK;
 }
@@ -392,40 +450,43 @@ gpsoc_status sync_state(gpsoc_problem* p) {
   return GPSOC_OK;
 }
 
+template <class T>
 gpsoc_status build_graph(gpsoc_problem* p, int level, const OptsDev& o) {
-  if (p->graph && p->graph_level == level && std::memcmp(&p->graph_opts, &o, sizeof(o)) == 0) return GPSOC_OK;
-  if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+  const int k = (sizeof(T) == 8) ? 0 : 1;
+  if (p->graph[k] && p->graph_level[k] == level && std::memcmp(&p->graph_opts[k], &o, sizeof(o)) == 0) return GPSOC_OK;
+  if (p->graph[k]) { cudaGraphExecDestroy(p->graph[k]); p->graph[k] = nullptr; }
   cudaGraph_t gr;
   Tracker tr;
   tr.stream = p->stream;
-  p->tr = &tr;
   CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-  gpsoc_status s = enqueue_iteration<double>(p, level, p->b64, 0, o, 0);
-  if (s == GPSOC_OK) s = enqueue_iteration<double>(p, level, p->b64, 1, o, 0);
+  p->tr = &tr;
+  gpsoc_status s = enqueue_iteration<T>(p, level, bufs<T>(p), 0, o, k);
+  if (s == GPSOC_OK) s = enqueue_iteration<T>(p, level, bufs<T>(p), 1, o, k);
   cudaError_t e = cudaStreamEndCapture(p->stream, &gr);
   p->tr = nullptr;
-  p->graph_kernels = tr.count;
+  p->graph_kernels[k] = tr.count;
   if (s != GPSOC_OK) { if (e == cudaSuccess) cudaGraphDestroy(gr); return s; }
   if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&p->graph, gr, 0);
+  e = cudaGraphInstantiate(&p->graph[k], gr, 0);
   cudaGraphDestroy(gr);
   if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  p->graph_level = level;
-  p->graph_opts = o;
+  p->graph_level[k] = level;
+  p->graph_opts[k] = o;
   return GPSOC_OK;
 }
 
-gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level) {
-  gpsoc_status s = init_level(p, level, first_level);
-  if (s != GPSOC_OK) return s;
-  s = build_graph(p, level, o);
+// replay the iteration graph of precision T until every solve has stopped
+template <class T>
+gpsoc_status iterate_until_done(gpsoc_problem* p, int level, const OptsDev& o, int check_every) {
+  const int k = (sizeof(T) == 8) ? 0 : 1;
+  gpsoc_status s = build_graph<T>(p, level, o);
   if (s != GPSOC_OK) return s;
   const int pairs = (check_every + 1) / 2;
   const long long cap = (long long)o.max_iter + 4;
   for (long long it = 0; it <= cap; it += 2 * pairs) {
-    for (int k = 0; k < pairs; ++k) {
-      CK(cudaGraphLaunch(p->graph, p->stream));
-      p->launches += p->graph_kernels;
+    for (int r = 0; r < pairs; ++r) {
+      CK(cudaGraphLaunch(p->graph[k], p->stream));
+      p->launches += p->graph_kernels[k];
     }
     s = sync_state(p);
     if (s != GPSOC_OK) return s;
@@ -434,6 +495,61 @@ gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_
     if (!any) return GPSOC_OK;
   }
   return GPSOC_OK;
+}
+
+gpsoc_status ensure_fp32(gpsoc_problem* p) {
+  if (p->b32.Phi) return GPSOC_OK;
+  const Geo g = make_geo(p, 0);
+  const size_t arr = sizeof(float2) * (size_t)p->batch * 3 * g.npts;
+  float2** slots[] = {&p->b32.Phi, &p->b32.HPhi, &p->b32.R[0], &p->b32.R[1], &p->b32.P[0], &p->b32.P[1],
+                      &p->b32.Z, &p->b32.D, &p->b32.A, &p->b32.B, &p->b32.W, &p->b32.G};
+  for (float2** sl : slots) {
+    if (cudaMalloc(sl, arr) != cudaSuccess) { cudaGetLastError(); return fail(GPSOC_ENOMEM, "device allocation failed (FP32 set)"); }
+  }
+  return GPSOC_OK;
+}
+
+// FP64 state -> FP32 working copy (or back)
+gpsoc_status convert_state(gpsoc_problem* p, int level, bool to32) {
+  const Geo g = make_geo(p, level);
+  const long long cnt = (long long)p->batch * 3 * g.npts;
+  if (to32) launch_convert<float>(p->b64.Phi, 0, p->b32.Phi, cnt, p->stream);
+  else launch_convert<double>(p->b32.Phi, 1, p->b64.Phi, cnt, p->stream);
+  mark(p, "convert");
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+// One multigrid level.  FP64: PCG to the stopping rule.  MIXED: PCG in FP32
+// arrays (FP64 reductions and scalars) until the energy change falls below
+// fp32_rel * |E| or Algorithm 2 finds no decrease (the FP32 rounding floor),
+// then PCG in FP64 from that iterate (beta restarted) to the stopping rule.
+gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level,
+                       int precision, double fp32_rel) {
+  gpsoc_status s;
+  if (precision == GPSOC_MIXED) {
+    s = ensure_fp32(p);
+    if (s != GPSOC_OK) return s;
+    s = convert_state(p, level, true);
+    if (s != GPSOC_OK) return s;
+    s = init_level(p, level, first_level);
+    if (s != GPSOC_OK) return s;
+    OptsDev o32 = o;
+    o32.stop = GPSOC_STOP_ENERGY;
+    o32.res_tol = 0.0;
+    o32.tol_rel = fp32_rel;
+    o32.phase32 = 1;
+    s = iterate_until_done<float>(p, level, o32, check_every);
+    if (s != GPSOC_OK) return s;
+    s = convert_state(p, level, false);
+    if (s != GPSOC_OK) return s;
+    s = init_level(p, level, false);
+    if (s != GPSOC_OK) return s;
+    return iterate_until_done<double>(p, level, o, check_every);
+  }
+  s = init_level(p, level, first_level);
+  if (s != GPSOC_OK) return s;
+  return iterate_until_done<double>(p, level, o, check_every);
 }
 
 gpsoc_status normalize(gpsoc_problem* p, int level) {
@@ -484,6 +600,7 @@ void fill_results(const gpsoc_problem* p, gpsoc_result* r, int levels) {
   for (int i = 0; i < p->batch; ++i) {
     const SolveState& S = p->h_st[i];
     gpsoc_result& o = r[i];
+    for (int k = 0; k < 8; ++k) o.level_iters[k] = (i < (int)p->level_iters.size() && k < (int)p->level_iters[i].size()) ? p->level_iters[i][k] : 0;
     o.status = S.status;
     if (S.status == GPSOC_OK && S.active) o.status = GPSOC_ENOTCONV;
     o.iters = S.iters;
@@ -580,11 +697,18 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
   }
   // partial-sum stride: the largest blocks-per-solve of any pass at the finest level
   Launch lc{};
-  p->pmax = row_blocks_per_solve<double>(g, lc);
-  for (int ax = 1; ax < p->dim; ++ax) p->pmax = std::max(p->pmax, col_blocks_per_solve<double>(g, ax, lc));
+  p->pmax = 1;
+  for (int lev = 0; lev <= p->max_level; ++lev) {
+    const Geo gl = make_geo(p, lev);
+    p->pmax = std::max(p->pmax, std::max(row_blocks_per_solve<double>(gl, lc), row_blocks_per_solve<float>(gl, lc)));
+    for (int ax = 1; ax < p->dim; ++ax)
+      p->pmax = std::max(p->pmax, std::max(col_blocks_per_solve<double>(gl, ax, lc), col_blocks_per_solve<float>(gl, ax, lc)));
+  }
   if (cudaMalloc(&p->d_part, sizeof(double) * (size_t)batch * NSLOT * p->pmax) != cudaSuccess)
     return bail(GPSOC_ENOMEM, "device allocation failed");
   if (cudaMalloc(&p->d_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMalloc(&p->d_cnt, sizeof(unsigned) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMemset(p->d_cnt, 0, sizeof(unsigned) * batch) != cudaSuccess) return bail(GPSOC_ECUDA, "memset failed");
   if (cudaMemset(p->d_st, 0, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ECUDA, "memset failed");
   if (cudaMallocHost(&p->h_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "host allocation failed");
   if (cudaMalloc(&p->d_scale, sizeof(double) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
@@ -599,7 +723,9 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
   for (int lev = 0; lev <= p->max_level; ++lev) {
     for (int i = 0; i < p->dim; ++i) {
       const double2* tw;
-      if (twiddles(p, p->n[i] >> lev, &tw) != GPSOC_OK) return bail(GPSOC_ENOMEM, "twiddle setup failed");
+      const float2* tw32;
+      if (twiddles(p, p->n[i] >> lev, &tw) != GPSOC_OK || twiddles(p, p->n[i] >> lev, &tw32) != GPSOC_OK)
+        return bail(GPSOC_ENOMEM, "twiddle setup failed");
     }
   }
   if (trap->kind == GPSOC_TRAP_USER) {
@@ -614,13 +740,18 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
 void gpsoc_destroy(gpsoc_problem* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (int k = 0; k < 2; ++k) if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
   double2* arrs[] = {p->b64.Phi, p->b64.HPhi, p->b64.R[0], p->b64.R[1], p->b64.P[0], p->b64.P[1],
                      p->b64.Z, p->b64.D, p->b64.A, p->b64.B, p->b64.W, p->b64.G};
   for (double2* a : arrs) if (a) cudaFree(a);
+  float2* arrs32[] = {p->b32.Phi, p->b32.HPhi, p->b32.R[0], p->b32.R[1], p->b32.P[0], p->b32.P[1],
+                      p->b32.Z, p->b32.D, p->b32.A, p->b32.B, p->b32.W, p->b32.G};
+  for (float2* a : arrs32) if (a) cudaFree(a);
   for (auto& kv : p->tw64) cudaFree(kv.second);
+  for (auto& kv : p->tw32) cudaFree(kv.second);
   if (p->d_part) cudaFree(p->d_part);
   if (p->d_st) cudaFree(p->d_st);
+  if (p->d_cnt) cudaFree(p->d_cnt);
   if (p->h_st) cudaFreeHost(p->h_st);
   if (p->d_scale) cudaFree(p->d_scale);
   if (p->d_tmp) cudaFree(p->d_tmp);
@@ -712,13 +843,20 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
   const OptsDev o = make_opts(opts);
   const int check = opts->check_every > 0 ? opts->check_every : 16;
   gpsoc_status s = GPSOC_OK;
+  p->level_iters.assign(p->batch, std::vector<int>());
+  std::vector<int> done(p->batch, 0);
   for (int lev = levels - 1; lev >= 0; --lev) {
     if (lev < p->level) {
       s = prolong_impl(p, lev + 1);
       if (s != GPSOC_OK) return s;
     }
-    s = run_level(p, lev, o, check, lev == levels - 1);
+    s = run_level(p, lev, o, check, lev == levels - 1, opts->precision,
+                  opts->fp32_switch > 0 ? opts->fp32_switch : 1e-11);
     if (s != GPSOC_OK) return s;
+    for (int i = 0; i < p->batch; ++i) {
+      p->level_iters[i].push_back(p->h_st[i].total_iters - done[i]);
+      done[i] = p->h_st[i].total_iters;
+    }
   }
   s = sync_state(p);
   if (s != GPSOC_OK) return s;
@@ -746,8 +884,13 @@ gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
     s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
     if (s != GPSOC_OK) return s;
   }
+  if (iters > 0) {
+    s = flush_pending<double>(p, p->level, p->b64, (iters - 1) & 1);
+    if (s != GPSOC_OK) return s;
+  }
   s = sync_state(p);
   if (s != GPSOC_OK) return s;
+  p->level_iters.assign(p->batch, std::vector<int>());
   if (results) fill_results(p, results, 1);
   return GPSOC_OK;
 }
@@ -823,7 +966,7 @@ gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, const double* r, double* out)
   if (s != GPSOC_OK) return s;
   a.gate = GATE_ALL;
   a.given_r = 1;
-  run_pre_chain<double>(p, a, B, B.D, B.Phi, B.R[0], nullptr, B.Z, false, nullptr);
+  run_pre_chain<double>(p, a, B, B.D, B.Phi, B.R[0], nullptr, B.Z, 0);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, B.Z, bytes, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
@@ -841,18 +984,22 @@ gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* t
   const Geo g = make_geo(p, p->level);
   const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
   Bufs<double>& B = p->b64;
-  CK(cudaMemcpyAsync(B.D, P, bytes, cudaMemcpyHostToDevice, p->stream));
+  // the P chain forms P = -z + beta P_prev - cproj Phi: pass z = -P with beta = cproj = 0
+  std::vector<double> negP(2 * (size_t)p->batch * 3 * g.npts);
+  for (size_t i = 0; i < negP.size(); ++i) negP[i] = -P[i];
+  CK(cudaMemcpyAsync(B.Z, negP.data(), bytes, cudaMemcpyHostToDevice, p->stream));
   double* d_theta = p->d_tmp;
   double* d_out = p->d_tmp + n_theta;
   if (n_theta) CK(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, p->stream));
   // cproj = 0 so that P is used as given
-  for (int i = 0; i < p->batch; ++i) p->h_st[i].cproj = 0.0;
+  for (int i = 0; i < p->batch; ++i) { p->h_st[i].cproj = 0.0; p->h_st[i].beta = 0.0; }
   CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
   ChainArgs<double> a;
   s = chain_args<double>(p, p->level, a);
   if (s != GPSOC_OK) return s;
   a.gate = GATE_ALL;
-  run_p_chain<double>(p, a, B, B.D, B.Phi, B.HPhi, B.P[0]);
+  run_p_chain<double>(p, a, B, B.Z, nullptr, B.Phi, B.HPhi, B.P[0], 0);
+  CK(cudaStreamSynchronize(p->stream));
   ScalarArgs x = scalar_args(p, p->level, PH_MODEL, g);
   x.force = 1;
   x.thetas = d_theta;
@@ -891,11 +1038,20 @@ gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   p->tr = &tr;
   size_t per = 0;
   std::vector<size_t> starts;
+  const bool f32 = (opts->precision == GPSOC_MIXED);
+  if (f32) {
+    p->tr = nullptr;
+    s = ensure_fp32(p);
+    if (s == GPSOC_OK) s = convert_state(p, p->level, true);
+    p->tr = &tr;
+  }
   for (int k = 0; k < iters && s == GPSOC_OK; ++k) {
     starts.push_back(tr.evs.size());
     tr.start();
-    s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
+    if (f32) s = enqueue_iteration<float>(p, p->level, p->b32, k & 1, o, 1);
+    else s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
   }
+  const int last_par = (iters - 1) & 1;
   p->tr = nullptr;
   p->launches += tr.count;
   if (s == GPSOC_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) s = fail(GPSOC_ECUDA, "profile sync failed");
@@ -914,6 +1070,10 @@ gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
     }
   }
   for (cudaEvent_t e : tr.evs) cudaEventDestroy(e);
+  if (s == GPSOC_OK) {
+    s = f32 ? flush_pending<float>(p, p->level, p->b32, last_par) : flush_pending<double>(p, p->level, p->b64, last_par);
+    if (s == GPSOC_OK && f32) s = convert_state(p, p->level, false);
+  }
   return s;
 }
 

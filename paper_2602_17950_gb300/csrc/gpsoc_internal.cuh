@@ -39,6 +39,7 @@ struct Geo {
   int n[3];         // nx, ny, nz (nz = 1 in 2D)
   int log2n[3];
   double L[3], h[3];
+  double piL[3];    // pi / L per axis: wavenumber of index k is p * piL with p = k or k - n
   long long npts;   // points of one component
   double dV;        // h^d
 };
@@ -61,7 +62,8 @@ struct SolveState {
   int reset;        // Algorithm 2 Step 2 asked for beta = 0 in this iteration
   int beta_resets, halvings;
   int fp32_iters, fp64_iters;
-  int pad0, pad1;
+  int pending;      // an accepted step waits to be applied by the next iteration's first pass
+  int pad1;
   // observables of the current iterate
   double E, mu, Q;          // energy, chemical potential, <H_lin Phi, Phi>
   double rho2, F2;          // sum rho^2, sum |F|^2 (times dV)
@@ -82,6 +84,8 @@ struct OptsDev {
   double theta_trial, sigma;
   int max_halvings;
   int no_stop;      // gpsoc_iterate: run without stopping tests
+  int phase32;      // FP32 phase of a mixed solve: stagnation / iteration cap end the phase, not the solve
+  double tol_rel;   // energy stop: |dE| < tol + tol_rel * |E|
 };
 
 // reduction slots (per solve); partial sums live in part[(s * NSLOT + slot) * pmax + block]
@@ -97,13 +101,27 @@ enum Slot {
   SL_HPP, SL_HPHIP, SL_RPHI,                      // <H_lin P,P>, Re<H Phi, P>, Re<P, Phi>
   SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,         // rho cross integrals
   SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP,         // spin cross integrals
-  SL_DPHIINF,                                     // max |Phi_new - Phi|
+  SL_DPHIINF,                                     // max |Phi_new - Phi|^2
   SL_NORM,                                        // sum |phi|^2 for normalisation
+  SL_HD, SL_ZPHI, SL_HZ,                          // Re<H Phi, D>, Re<z, Phi>, Re<H Phi, z>
   NSLOT
 };
 
-// gate of a chain kernel: which per-solve flag must be set for the block to run
-enum Gate { GATE_ALL = 0, GATE_ACTIVE = 1, GATE_RESET = 2 };
+// gate of a kernel: which per-solve flag must be set for the block to run
+enum Gate { GATE_ALL = 0, GATE_ACTIVE = 1, GATE_RESET = 2, GATE_PENDING = 3 };
+
+// what the scalar steps read: state, parameters, block partial sums and sizes
+struct ScalarCtx {
+  SolveState* st;
+  const PhysDev* phys;
+  const double* part;
+  int pmax;
+  int nb_row, nb_col;   // blocks per solve of the row passes and of the last column pass
+  long long npts;
+  double dV;
+  OptsDev opts;
+  int flags;            // 2 = count accepted steps as FP32 iterations
+};
 
 template <class T>
 struct ChainArgs {
@@ -120,66 +138,124 @@ struct ChainArgs {
   int nsolve;
   double scale;       // extra scale factor (prolongation, normalisation)
   int given_r;        // ROW_FWD_PRE: in0 already holds r (mu taken as 0)
+  int fuse;           // the last block of the pass runs the scalar step that consumes its sums
+  unsigned* cnt;      // per-solve block arrival counters (fused scalar steps)
+  ScalarCtx sc;
 };
 
 __device__ __forceinline__ bool gate_ok(const SolveState* st, int gate, int s) {
   if (gate == GATE_ALL) return true;
   if (gate == GATE_ACTIVE) return st[s].active != 0;
+  if (gate == GATE_PENDING) return st[s].active != 0 && st[s].pending != 0;
   return st[s].active != 0 && st[s].reset != 0;
 }
 
-// wavenumber of FFT index k on an axis of n points and half-width L
-__device__ __forceinline__ double wavenum(int k, int n, double L) {
-  int p = (k < (n >> 1)) ? k : k - n;
-  return 3.14159265358979323846 * (double)p / L;
+// True in every thread of the block that arrives last among the `bps` blocks of
+// solve s (threadfence-reduction pattern: partial sums written before the
+// arrival are visible to the last block).  The last block resets the counter.
+__device__ __forceinline__ bool last_block(unsigned* cnt, int s, int bps, int* flag_smem) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(cnt + s, 1u);
+    *flag_smem = (prev == (unsigned)bps - 1u);
+  }
+  __syncthreads();
+  const bool last = *flag_smem != 0;
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) cnt[s] = 0u;
+  }
+  return last;
 }
 
-__device__ __forceinline__ double trap_value(const TrapDev& t, const Geo& g, int ix, int iy, int iz,
-                                             long long idx) {
-  double x = -g.L[0] + ix * g.h[0];
-  double y = -g.L[1] + iy * g.h[1];
-  double v = t.half_g2[0] * x * x + t.half_g2[1] * y * y;
-  double r2 = x * x + y * y;
+// wavenumber v_p = pi p / L of FFT index k on an axis of n points (Section 3.2),
+// evaluated in the working precision W of the kernel
+template <class W>
+__device__ __forceinline__ W wavenum(int k, int n, double piL) {
+  const int p = (k < (n >> 1)) ? k : k - n;
+  return (W)p * (W)piL;
+}
+
+// trapping potential at grid point (ix, iy, iz) in the working precision W
+template <class W>
+__device__ __forceinline__ W trap_value(const TrapDev& t, const Geo& g, int ix, int iy, int iz, long long idx) {
+  const W x = (W)(-g.L[0]) + (W)ix * (W)g.h[0];
+  const W y = (W)(-g.L[1]) + (W)iy * (W)g.h[1];
+  W v = (W)t.half_g2[0] * x * x + (W)t.half_g2[1] * y * y;
+  W r2 = x * x + y * y;
   if (g.d == 3) {
-    double z = -g.L[2] + iz * g.h[2];
-    v += t.half_g2[2] * z * z;
+    const W z = (W)(-g.L[2]) + (W)iz * (W)g.h[2];
+    v += (W)t.half_g2[2] * z * z;
     r2 += z * z;
   }
-  v += t.quad * r2 + t.quart * r2 * r2;
-  if (t.userV) v += t.userV[idx];
+  v += (W)t.quad * r2 + (W)t.quart * r2 * r2;
+  if (t.userV) v += (W)t.userV[idx];
   return v;
 }
 
 // ------------------------------------------------------------------ block reductions (deterministic)
-// Sums K doubles over the block in a fixed order: warp shuffle tree, then warps
-// in index order.  scratch: >= 32 * K doubles of shared memory.  Result valid in
-// thread 0.  IS_MAX selects max instead of sum.
+// FP64 block reductions in a fixed order.  FP64 issue slots are scarce on this
+// part (about 1/64 of FP32), so a multi-value reduction does not run one
+// shuffle tree per value (5 adds per lane per value): a warp first performs a
+// reduce-scatter over 16 value slots -- at each of four halving steps a lane
+// keeps one half of its values and adds the partner lane's copy of that half --
+// so that every lane ends with one slot (16 adds per lane in total), then the
+// two half-warps are added, and the warps are added in index order.
+// scratch: >= 16 * (blockDim.x / 32) + 16 doubles.  Every thread receives the
+// K results in v.  is_max is honoured for K == 1 only (multi-value calls sum).
 template <int K>
 __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, const bool (&is_max)[K]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
+  __syncthreads();  // scratch may alias shared memory the caller used just before
+  if (K == 1) {
+    double x = v[0];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      double o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = is_max[k] ? fmax(v[k], o) : v[k] + o;
+      const double o = __shfl_down_sync(0xffffffffu, x, off);
+      x = is_max[0] ? fmax(x, o) : x + o;
+    }
+    if (lane == 0) scratch[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = scratch[0];
+      for (int w = 1; w < nw; ++w) acc = is_max[0] ? fmax(acc, scratch[w]) : acc + scratch[w];
+      scratch[nw] = acc;
+    }
+    __syncthreads();
+    v[0] = scratch[nw];
+    return;
+  }
+  static_assert(K <= 16, "block_reduce handles at most 16 values");
+  double x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = (k < K) ? v[k] : 0.0;
+  // reduce-scatter: after the step with offset ofs each lane holds hv/2 slots
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    const int ofs = 1 << st, half = 8 >> st;
+    const bool up = (lane & ofs) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double keep = up ? x[i + half] : x[i];
+      const double send = up ? x[i] : x[i + half];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, ofs);
     }
   }
+  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 16);
+  // lane l (< 16) now holds slot 8 b0 + 4 b1 + 2 b2 + b3 of its bits b0..b3
+  const int slot = ((lane & 1) << 3) | ((lane & 2) << 1) | ((lane & 4) >> 1) | ((lane & 8) >> 3);
+  if (lane < 16) scratch[warp * 16 + slot] = x[0];
   __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) scratch[warp * K + k] = v[k];
+  double* res = scratch + 16 * nw;
+  if (threadIdx.x < K) {
+    double acc = scratch[threadIdx.x];
+    for (int w = 1; w < nw; ++w) acc += scratch[w * 16 + threadIdx.x];
+    res[threadIdx.x] = acc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double acc = scratch[k];
-      for (int w = 1; w < nw; ++w) acc = is_max[k] ? fmax(acc, scratch[w * K + k]) : acc + scratch[w * K + k];
-      v[k] = acc;
-    }
-  }
-  __syncthreads();
+  for (int k = 0; k < K; ++k) v[k] = res[k];
 }
 
 // ------------------------------------------------------------------ shared-memory FFT
@@ -255,14 +331,15 @@ template <class T> struct Chain;  // kernels of one precision (defined in chain.
 
 // Launchers implemented in chain.cu (explicitly instantiated for double, float).
 enum RowMode {
-  ROW_FWD_PLAIN = 0,   // out0 = F_x(in0)
+  ROW_FWD_PLAIN = 0,   // out0 = F_x(in0); with ROW_FWD_UPD first applies a pending step to in0 (= out1)
   ROW_FWD_PROJ,        // P = in0 - cproj * in1 -> out1; out0 = F_x(P); reduce ||P||^2
   ROW_FWD_PRE,         // r = in0 - mu in1 -> out1; out0 = F_x(s * r); reduce max|r|
   ROW_INV_H,           // out0 = H(Phi) from T' (in0), G (in1), Phi (in2); energy reductions
   ROW_INV_P,           // reductions of the step model from T' (in0), G (in1), P (in2), Phi (in3), HPhi (in4)
   ROW_INV_PRE,         // z = s * F_x^-1(in0)/npts -> out0; reduce <r,z>, <r_prev,z> (in2 = r, in3 = r_prev, in1 = Phi)
   ROW_INV_PLAIN,       // out0 = scale * F_x^-1(in0)
-  ROW_INV_LIN          // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
+  ROW_INV_LIN,         // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
+  ROW_FWD_UPD          // Phi (in0, written back to out1) <- pending step with P (in2); out0 = F_x(Phi)
 };
 enum ColMode {
   COL_FWD = 0,         // out0 = F_axis(in0)

@@ -10,10 +10,9 @@ enum Phase {
   PH_OBS,           // E, mu, alpha, masses from the H-chain partials
   PH_RES,           // max |r| and the stopping test
   PH_BETA,          // Polak-Ribiere+ beta
-  PH_CPROJ,         // Re<D, Phi>
-  PH_STEP,          // Algorithm 2 (step model, reset decision, backtracking, update coefficients)
-  PH_CPROJ_RESET,   // as PH_CPROJ / PH_STEP for solves in the beta = 0 re-run
-  PH_STEP_RESET,
+  PH_CPROJ,         // Re<D, Phi> and the beta = 0 decision of Algorithm 2 Step 2
+  PH_STEP,          // Algorithm 2 (step model, backtracking, update coefficients)
+  PH_CLEAR,         // drop the pending-step flag
   PH_NORM,          // 1/sqrt(mass) per solve into norm_scale
   PH_MODEL          // a_n, b_n and E(theta) - E(0) at given angles into model_out
 };
@@ -40,8 +39,8 @@ enum ElemMode { EL_DIR = 0, EL_UPDATE, EL_MASS, EL_SCALE };
 template <class T>
 struct ElemArgs {
   using C = cx_t<T>;
-  const SolveState* st;
-  const C* in0; const C* in1; const C* in2;
+  SolveState* st;
+  const C* in0; const C* in1; const C* in2; const C* in3;
   C* out0;
   double* part; int pmax;
   const double* scalev;
@@ -49,6 +48,9 @@ struct ElemArgs {
   int bps;            // blocks per solve (divides npts)
   int nsolve;
   int gate;
+  int fuse;           // EL_DIR: the last block runs the PH_CPROJ step
+  unsigned* cnt;
+  ScalarCtx sc;
 };
 
 void launch_scalar(const ScalarArgs& a, cudaStream_t st);

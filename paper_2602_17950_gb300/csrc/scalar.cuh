@@ -1,0 +1,230 @@
+// Scalar steps of the PCG iteration (Section 3.1, Algorithms 1 and 2), run by one
+// thread block per solve: either by a separate kernel or fused into the last
+// block of the array pass that produced their sums.  Every thread of the block
+// calls the function (block reductions); thread 0 updates the solve's state.
+// Sums of block partials are taken in a fixed order (deterministic).
+#pragma once
+
+#include "gpsoc_internal.cuh"
+
+namespace gpsoc {
+
+// K slot totals (sums over the nb block partials of solve s); every thread gets them
+template <int K>
+__device__ __forceinline__ void slot_totals(const ScalarCtx& X, int s, const int (&slots)[K], int nb, double (&v)[K],
+                                            double* scratch) {
+  const bool mx[K] = {};
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double* p = X.part + ((long long)s * NSLOT + slots[k]) * X.pmax;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(p + b);
+    v[k] = acc;
+  }
+  block_reduce<K>(v, scratch, mx);
+}
+
+__device__ __forceinline__ double slot_max(const ScalarCtx& X, int s, int slot, int nb, double* scratch) {
+  double v[1] = {0.0};
+  const double* p = X.part + ((long long)s * NSLOT + slot) * X.pmax;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v[0] = fmax(v[0], __ldcg(p + b));
+  const bool mx[1] = {true};
+  block_reduce<1>(v, scratch, mx);
+  return v[0];
+}
+
+__device__ __forceinline__ void deactivate(SolveState& S, int status) {
+  S.active = 0;
+  if (S.status == GPSOC_OK) S.status = status;
+}
+
+// E, mu (Eqs. energy, muphi), alpha_l (Eq. PreCnstAlpha), masses of the current iterate
+__device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratch) {
+  SolveState& S = X.st[s];
+  const PhysDev ph = X.phys[s];
+  double kin[3], v[12];
+  const int kslots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
+  slot_totals<3>(X, s, kslots, X.nb_col, kin, scratch);
+  const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
+  slot_totals<12>(X, s, slots, X.nb_row, v, scratch);
+  const bool had_step = S.pending != 0;
+  double dphi = 0.0;
+  if (had_step) dphi = slot_max(X, s, SL_DPHIINF, X.nb_row, scratch);
+  if (threadIdx.x != 0) return;
+  const double dV = X.dV;
+  S.Q = dV * v[0];
+  S.rho2 = dV * v[1];
+  S.F2 = dV * v[2];
+  S.E = S.Q + 0.5 * ph.c0 * S.rho2 + 0.5 * ph.c1 * S.F2;
+  S.mu = S.Q + ph.c0 * S.rho2 + ph.c1 * S.F2;
+  double amax = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    S.alpha[c] = dV * (kin[c] / (double)X.npts + v[3 + c] + ph.c0 * v[6 + c]);
+    S.mass[c] = dV * v[9 + c];
+    amax = fmax(amax, fabs(S.alpha[c]));
+  }
+  const double floor_a = 1e-12 * amax + 1e-300;
+  for (int c = 0; c < 3; ++c) S.alpha[c] = fmax(S.alpha[c], floor_a);
+  if (had_step) S.dphi_inf = sqrt(dphi);
+  S.pending = 0;
+  if (!isfinite(S.E) || !isfinite(S.mu) || !isfinite(S.alpha[0] + S.alpha[1] + S.alpha[2]))
+    deactivate(S, GPSOC_ENONFINITE);
+}
+
+// max_l ||r_l||_inf and the stopping test (Eqs. stop1-stop3)
+__device__ __forceinline__ void sc_res(const ScalarCtx& X, int s, double* scratch) {
+  SolveState& S = X.st[s];
+  const double rinf = slot_max(X, s, SL_RINF, X.nb_row, scratch);
+  if (threadIdx.x != 0) return;
+  const OptsDev& O = X.opts;
+  S.res_inf = rinf;
+  if (!isfinite(rinf)) { deactivate(S, GPSOC_ENONFINITE); return; }
+  if (O.no_stop) return;
+  if (S.iters >= 1 || O.stop == GPSOC_STOP_RES) {
+    bool conv;
+    if (O.stop == GPSOC_STOP_ENERGY) conv = fabs(S.dE_last) < O.tol + O.tol_rel * fabs(S.E);
+    else if (O.stop == GPSOC_STOP_RES) conv = rinf < O.tol;
+    else conv = S.dphi_inf < O.tol;
+    if (conv && O.res_tol > 0.0) conv = rinf < O.res_tol;
+    if (conv) { S.active = 0; return; }
+  }
+  if (S.iters >= O.max_iter) {
+    if (O.phase32) S.active = 0;
+    else deactivate(S, GPSOC_ENOTCONV);
+  }
+}
+
+// Polak-Ribiere+ beta = max(Re<r - r_prev, P r> / Re<r_prev, P_prev r_prev>, 0)
+__device__ __forceinline__ void sc_beta(const ScalarCtx& X, int s, double* scratch) {
+  SolveState& S = X.st[s];
+  double w[2];
+  const int wslots[2] = {SL_RZ, SL_RPZ};
+  slot_totals<2>(X, s, wslots, X.nb_row, w, scratch);
+  if (threadIdx.x != 0) return;
+  const double dV = X.dV;
+  S.s_cur = dV * w[0];
+  double beta = 0.0;
+  if (!S.first) {
+    beta = (dV * w[0] - dV * w[1]) / S.s_prev;
+    if (!(beta > 0.0)) beta = 0.0;   // max(beta, 0), NaN -> 0
+  }
+  S.beta = beta;
+}
+
+// Tangent projection coefficient c = Re<D, Phi> (Eq. formula-project), and
+// Algorithm 2 Step 2 decided before the direction is transformed:
+// b_n has the sign of Re<H Phi, P> = Re<H Phi, D> - c mu, so when it is >= 0
+// for D = -P r + beta P_prev the step restarts from D = -P r (beta = 0).
+__device__ __forceinline__ void sc_cproj(const ScalarCtx& X, int s, double* scratch) {
+  SolveState& S = X.st[s];
+  double w[4];
+  const int wslots[4] = {SL_DPHI, SL_HD, SL_ZPHI, SL_HZ};
+  slot_totals<4>(X, s, wslots, X.nb_row, w, scratch);
+  if (threadIdx.x != 0) return;
+  const double dV = X.dV;
+  const double cD = dV * w[0], hD = dV * w[1];
+  if (S.beta != 0.0 && !(hD - cD * S.mu < 0.0)) {
+    S.beta = 0.0;
+    S.beta_resets++;
+    S.cproj = -dV * w[2];   // D = -z: Re<D, Phi> = -Re<z, Phi>
+  } else {
+    S.cproj = cD;
+  }
+}
+
+// E(cos t Phi + sin t P/||P||) - E(Phi) from the reduced integrals (unnormalised P):
+// quadratic part -s^2 Q + 2cs/|P| Re<H_lin Phi,P> + s^2/|P|^2 <H_lin P,P>, interaction
+// part from rho_t - rho = u rho_Phi + w1 R + w2 rho_P (u = -s^2, w1 = 2cs/|P|, w2 = s^2/|P|^2)
+// and the same for the spin density (Section 3.1, the explicit form of E(theta)).
+__device__ __forceinline__ double energy_change(const SolveState& S, double c0, double c1, double theta) {
+  const double nP2 = S.P2, nP = sqrt(nP2);
+  const double QFP = S.HPhiP - c0 * S.I[1] - c1 * S.J[1];
+  double sn, cs;
+  sincos(theta, &sn, &cs);
+  const double u = -sn * sn, w1 = 2.0 * cs * sn / nP, w2 = sn * sn / nP2;
+  const double quad = u * S.Q + w1 * QFP + w2 * S.HPP;
+  const double* I = S.I;
+  const double* J = S.J;
+  const double rl = u * I[0] + w1 * I[1] + w2 * I[2];
+  const double rq = u * u * I[0] + w1 * w1 * I[3] + w2 * w2 * I[5] + 2.0 * u * w1 * I[1] + 2.0 * u * w2 * I[2] +
+                    2.0 * w1 * w2 * I[4];
+  const double fl = u * J[0] + w1 * J[1] + w2 * J[2];
+  const double fq = u * u * J[0] + w1 * w1 * J[3] + w2 * w2 * J[5] + 2.0 * u * w1 * J[1] + 2.0 * u * w2 * J[2] +
+                    2.0 * w1 * w2 * J[4];
+  return quad + 0.5 * c0 * (2.0 * rl + rq) + 0.5 * c1 * (2.0 * fl + fq);
+}
+
+// gather the step-model sums of the P chain into the state; returns (a_n, b_n) (Eqs. an, bn)
+__device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scratch) {
+  SolveState& S = X.st[s];
+  double v[14];
+  const int slots[14] = {SL_P2, SL_HPP, SL_HPHIP, SL_RPHI, SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,
+                         SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP};
+  slot_totals<14>(X, s, slots, X.nb_row, v, scratch);
+  if (threadIdx.x != 0) return;
+  const double dV = X.dV;
+  S.P2 = dV * v[0]; S.HPP = dV * v[1]; S.HPhiP = dV * v[2]; S.RPhi = dV * v[3];
+  for (int k = 0; k < 5; ++k) { S.I[k + 1] = dV * v[4 + k]; S.J[k + 1] = dV * v[9 + k]; }
+  S.I[0] = S.rho2; S.J[0] = S.F2;
+  const PhysDev ph = X.phys[s];
+  const double nP2 = S.P2;
+  // density frozen at Phi^n in H_l(P^n)
+  S.a = -S.mu + (S.HPP + ph.c0 * S.I[2] + ph.c1 * S.J[2]) / nP2 + 2.0 * (ph.c0 * S.I[3] + ph.c1 * S.J[3]) / nP2;
+  S.b = 2.0 * S.HPhiP / sqrt(nP2);
+}
+
+// Algorithm 2: step size from the quadratic model, backtracking on the exact
+// energy change, update coefficients of Eqs. formula-pcg / update (applied by
+// the next iteration's first pass).
+__device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scratch) {
+  step_sums(X, s, scratch);
+  if (threadIdx.x != 0) return;
+  SolveState& S = X.st[s];
+  const PhysDev ph = X.phys[s];
+  const OptsDev& O = X.opts;
+  const double a = S.a, b = S.b;
+  if (!isfinite(a) || !isfinite(b)) { deactivate(S, GPSOC_ENONFINITE); return; }
+  if (b > 0.0 || (b == 0.0 && a >= 0.0)) {
+    if (S.beta == 0.0) {
+      if (O.phase32) S.active = 0;   // rounding floor of the FP32 phase: hand over to FP64
+      else deactivate(S, GPSOC_ESTAGNATED);
+      return;
+    }
+    // the sign test before the transform missed by rounding: redo this step with
+    // beta = 0 in the next iteration (same Phi, same residual: Step 2 -> Step 1)
+    S.first = 1;
+    S.beta_resets++;
+    return;
+  }
+  double theta = (a > 0.0 && b < 0.0) ? -b / (2.0 * a) : O.theta_trial;
+  bool accepted = false;
+  double dE = 0.0;
+  for (int h = 0; h <= O.max_halvings; ++h) {
+    dE = energy_change(S, ph.c0, ph.c1, theta);
+    if (dE < 0.0) { accepted = true; break; }
+    theta *= O.sigma;
+    S.halvings++;
+  }
+  if (!accepted) {
+    if (O.phase32) S.active = 0;
+    else deactivate(S, GPSOC_ESTAGNATED);
+    return;
+  }
+  double sn, cs;
+  sincos(theta, &sn, &cs);
+  const double nP2 = S.P2, nP = sqrt(nP2);
+  S.theta = theta;
+  S.dE = dE;
+  S.dE_last = dE;
+  const double sp = sn / nP;
+  const double M = S.mass[0] + S.mass[1] + S.mass[2];
+  const double nrm2 = cs * cs * M + 2.0 * cs * sp * S.RPhi + sp * sp * nP2;
+  S.upd_c = cs; S.upd_s = sp; S.upd_scale = 1.0 / sqrt(nrm2);
+  S.pending = 1;
+  S.iters++; S.total_iters++;
+  if (X.flags & 2) S.fp32_iters++; else S.fp64_iters++;
+  S.first = 0;
+  S.s_prev = S.s_cur;
+}
+
+}  // namespace gpsoc

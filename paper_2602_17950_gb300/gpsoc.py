@@ -45,20 +45,22 @@ class Params(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("tol", C.c_double), ("res_tol", C.c_double),
                 ("max_iter", C.c_int), ("theta_trial", C.c_double), ("sigma", C.c_double),
-                ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int)]
+                ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int),
+                ("fp32_switch", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("total_iters", C.c_int), ("levels", C.c_int),
                 ("beta_resets", C.c_int), ("halvings", C.c_int), ("fp32_iters", C.c_int), ("fp64_iters", C.c_int),
                 ("energy", C.c_double), ("mu", C.c_double), ("mass", C.c_double * 3), ("res_inf", C.c_double),
-                ("dE_last", C.c_double)]
+                ("dE_last", C.c_double), ("level_iters", C.c_int * 8)]
 
     def as_dict(self):
         return {"status": status_name(self.status), "iters": self.iters, "total_iters": self.total_iters,
                 "levels": self.levels, "beta_resets": self.beta_resets, "halvings": self.halvings,
                 "fp32_iters": self.fp32_iters, "fp64_iters": self.fp64_iters, "energy": self.energy,
-                "mu": self.mu, "mass": list(self.mass), "res_inf": self.res_inf, "dE_last": self.dE_last}
+                "mu": self.mu, "mass": list(self.mass), "res_inf": self.res_inf, "dE_last": self.dE_last,
+                "level_iters": list(self.level_iters[:max(self.levels, 1)])}
 
 
 _lib = None
@@ -84,6 +86,7 @@ _PROTOS = {
     "gpsoc_profile": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "gpsoc_profile_name": (C.c_char_p, [C.c_void_p, C.c_int]),
     "gpsoc_kernel_launches": (C.c_uint64, [C.c_void_p]),
+    "gpsoc_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gpsoc_last_error": (C.c_char_p, []),
     "gpsoc_version": (C.c_char_p, []),
 }
@@ -121,6 +124,13 @@ def _current_stream():
     except Exception:
         pass
     return None
+
+
+def probe_peaks():
+    """(FP64, FP32) FMA throughput of the current device in TFLOP/s."""
+    a, b = C.c_double(0), C.c_double(0)
+    _check(library().gpsoc_probe_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 class Problem:
@@ -179,9 +189,9 @@ class Problem:
 
     @staticmethod
     def opts(precision=GPSOC_FP64, stop=GPSOC_STOP_ENERGY, tol=1e-12, res_tol=0.0, max_iter=100000,
-             theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0):
+             theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0, fp32_switch=0.0):
         return Opts(precision, stop, tol, res_tol, max_iter, theta_trial, sigma, max_halvings, cm_levels,
-                    check_every)
+                    check_every, fp32_switch)
 
     # -------------------------------------------------------------- state
     def set_initial(self, psi: np.ndarray, level=0):
@@ -198,8 +208,10 @@ class Problem:
         _check(library().gpsoc_set_initial_kind(self._h, k, level))
         self.level = level
 
-    def psi(self) -> np.ndarray:
-        out = np.empty(self.shape(), dtype=np.complex128)
+    def psi(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape(), dtype=np.complex128)
+        assert out.dtype == np.complex128 and out.flags.c_contiguous and out.size == np.prod(self.shape())
         _check(library().gpsoc_get_psi(self._h, _ptr(out)))
         return out
 

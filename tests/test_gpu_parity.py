@@ -266,3 +266,54 @@ def test_nonfinite_input_is_reported():
         p.set_initial(psi[None])
         r = p.solve(tol=1e-12)[0]
     assert r["status"] == "ENONFINITE"
+
+
+def test_mixed_precision_ground_state_matches_oracle():
+    # FP32 transforms + FP64 reductions, then FP64 polishing: same tolerances as FP64.
+    # An anisotropic trap removes the joint space-spin rotation symmetry of radial
+    # traps, so the minimiser (and its density) is unique up to the global phase.
+    n, L, par = (64, 64), (8.0, 8.0), (0.5, 0.5, 100.0, -1.0)
+    trap = {"kind": 0, "g": (1.0, 1.15)}
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    m = oracle_model(n, L, par, trap)
+    ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10))
+    with Problem(n, L, [par], trap=trap) as p:
+        p.set_initial(psi0[None])
+        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1)[0]
+        got = p.psi()[0]
+    assert res["fp32_iters"] > 0 and res["fp64_iters"] > 0
+    _assert_ground_state_parity(m, ref, res, got)
+
+
+def test_mixed_precision_radial_trap_invariants_match_oracle():
+    # radial trap (config-1 parameters): the minimiser is degenerate under joint
+    # spatial + spin rotation, so compare the invariant observables: E, mu, masses
+    n, L, par = (64, 64), (8.0, 8.0), (0.5, 0.5, 100.0, -1.0)
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    m = oracle_model(n, L, par)
+    ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10))
+    with Problem(n, L, [par]) as p:
+        p.set_initial(psi0[None])
+        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1)[0]
+    assert res["status"] == "OK"
+    assert res["energy"] == pytest.approx(ref.energy, rel=1e-10)
+    assert res["mu"] == pytest.approx(ref.mu, rel=1e-10)
+    np.testing.assert_allclose(res["mass"], ref.masses, atol=1e-8)
+
+
+def test_mixed_precision_cm_batch_matches_fp64():
+    n, L = (64, 64), (8.0, 8.0)
+    trap = {"kind": 0, "g": (1.0, 1.2)}
+    pars = [(0.3, 0.7, 200.0, -3.0), (0.6, 0.2, 80.0, 5.0)]
+    psis = np.stack([si.gaussian_guess((32, 32), L, 300 + k, vortex=True) for k in range(2)])
+    out = {}
+    for prec in (0, 1):
+        with Problem(n, L, pars, trap=trap) as p:
+            p.set_initial(psis, level=1)
+            out[prec] = (p.solve(tol=1e-12, res_tol=2e-10, cm_levels=2, precision=prec), p.psi())
+    for k in range(2):
+        r64, r32 = out[0][0][k], out[1][0][k]
+        assert r64["status"] == "OK" and r32["status"] == "OK"
+        assert r32["energy"] == pytest.approx(r64["energy"], rel=1e-10)
+        assert r32["mu"] == pytest.approx(r64["mu"], rel=1e-10)
+        assert np.max(np.abs(np.abs(out[1][1][k]) ** 2 - np.abs(out[0][1][k]) ** 2)) < 1e-8
