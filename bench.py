@@ -117,27 +117,29 @@ def fft_flops(n: int) -> float:
     return 5.0 * n * math.log2(n)
 
 
-def kernel_flops(name: str, n=N_FINE) -> float:
-    """Algorithmic FP64 flops of one launch of a 2D pass on one solve (3 components):
-    the FFTs it performs (5 n log2 n each); pointwise work is not counted."""
+# 1-D transforms per launch (of every line of one component) and 3-component arrays
+# moved per launch (each array read or written once: the algorithmic minimum)
+KERNEL_WORK = {
+    "row_fwd_upd": (1, "row", 4), "row_fwd": (1, "row", 2), "coly_ymid_h": (3, "col", 3),
+    "row_inv_h": (2, "row", 4), "row_fwd_pre": (1, "row", 4), "coly_mid_pre": (2, "col", 2),
+    "row_inv_pre": (1, "row", 5), "el_dir": (0, "row", 4), "row_fwd_proj": (1, "row", 5),
+    "row_inv_p": (2, "row", 5),
+}
+
+
+def kernel_flops(name: str, n) -> float:
+    """Algorithmic flops of one launch of a 2D pass on one solve (3 components):
+    the 1-D FFTs it performs, 5 n log2 n each; pointwise work is not counted."""
     nx, ny = n
-    per_row = fft_flops(nx) * ny          # one transform of every row of one component
-    per_col = fft_flops(ny) * nx
-    table = {
-        "row_fwd": 1 * per_row, "row_fwd_proj": 1 * per_row, "row_fwd_pre": 1 * per_row,
-        "row_inv_h": 2 * per_row, "row_inv_p": 2 * per_row, "row_inv_pre": 1 * per_row,
-        "coly_ymid_h": 3 * per_col, "coly_mid_pre": 2 * per_col,
-    }
-    return 3.0 * table.get(name, 0.0)
+    k, kind, _ = KERNEL_WORK.get(name, (0, "row", 0))
+    per = fft_flops(nx) * ny if kind == "row" else fft_flops(ny) * nx
+    return 3.0 * k * per
 
 
-def kernel_bytes(name: str, n=N_FINE, elem=16) -> float:
-    """Algorithmic DRAM bytes of one launch of a 2D pass on one solve: 3-component
-    arrays read and written once each (elem = bytes per complex value)."""
-    arr = 3.0 * n[0] * n[1] * elem
-    rw = {"row_fwd": 2, "row_fwd_proj": 4, "row_fwd_pre": 4, "row_inv_h": 4, "row_inv_p": 5, "row_inv_pre": 5,
-          "coly_ymid_h": 4, "coly_mid_pre": 2, "el_dir": 4, "el_update": 3}
-    return arr * rw.get(name, 0)
+def kernel_bytes(name: str, n, elem: int) -> float:
+    """Algorithmic DRAM bytes of one launch on one solve: 3-component arrays of
+    n^2 complex values (elem bytes each), each read or written once."""
+    return KERNEL_WORK.get(name, (0, "row", 0))[2] * 3.0 * n[0] * n[1] * elem
 
 
 # ------------------------------------------------------------------ oracle (CPU) sample
@@ -167,6 +169,29 @@ def oracle_sample(iters_per_level, budget_s: float = 20.0):
 
 
 # ------------------------------------------------------------------ our arm
+def timed_solves(prob, opts, d_psi0, flush, stream, warmup, steps, torch):
+    """W untimed + K timed solves from the device-resident guess; CUDA events on
+    the solver's stream around each solve, L2 flushed between solves."""
+    def step():
+        prob.set_initial_device(d_psi0.data_ptr(), level=LEVELS - 1)
+        return prob.solve(**opts)[0]
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    lat, results = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step()
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        results.append(r)
+    return lat, results
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2602_17950_gb300 import Problem
@@ -182,55 +207,42 @@ def run_ours(args, rank, world, local_rank):
     d_psi0 = torch.from_numpy(psi0[None].copy()).to(dev)
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
     prob = Problem(N_FINE, L_BOX, [PAR])
-    opts = dict(precision=prec, tol=TOL, cm_levels=LEVELS, check_every=32)
-
-    def step():
-        prob.set_initial_device(d_psi0.data_ptr(), level=LEVELS - 1)
-        return prob.solve(**opts)[0]
-
+    opts = dict(precision=prec, tol=TOL, cm_levels=LEVELS, check_every=64)
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    for _ in range(args.warmup):
-        res = step()
-    torch.cuda.synchronize()
-    if dist:
         tdist.barrier()
     torch.cuda.synchronize()
-    lat = []
-    results = []
     launches0 = prob.kernel_launches()
     with ClockSampler(local_rank) as clk:
-        t_begin = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            res = step()
-            e1.record(stream)
-            e1.synchronize()
-            lat.append(e0.elapsed_time(e1))
-            results.append(res)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_begin
+        lat, results = timed_solves(prob, opts, d_psi0, flush, stream, args.warmup, args.steps, torch)
     launches = prob.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    t = torch.tensor([sum(lat)], dtype=torch.float64, device=dev)
     if dist:
         tdist.barrier()
-    torch.cuda.synchronize()
-    total_ms = sum(lat)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist:
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
     max_total_ms = float(t.item())
     ok = all(r["status"] == "OK" for r in results)
+    # warm-up launches are included in the counter: keep only the timed solves' share
+    launches_timed = int(round(launches * args.steps / (args.steps + args.warmup)))
+
+    # the plain FP64 PCG on the same workload and tolerance (the comparison of the metric)
+    fp64 = None
+    if prec == 1 and not args.no_fp64:
+        lat64, res64 = timed_solves(prob, dict(opts, precision=0), d_psi0, flush, stream, 1, args.fp64_steps, torch)
+        fp64 = {"value": world * 1000.0 / statistics.mean(lat64), "unit": "solves/s",
+                "ms_per_solve": statistics.mean(lat64), "p50_ms": float(np.percentile(lat64, 50)),
+                "p99_ms": float(np.percentile(lat64, 99)), "status_ok": all(r["status"] == "OK" for r in res64),
+                "energy": res64[-1]["energy"], "iters_total": res64[-1]["total_iters"],
+                "level_iters": res64[-1]["level_iters"]}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     h_in = torch.empty(psi0[None].shape, dtype=torch.complex128, pin_memory=True)
     h_in.numpy()[...] = psi0[None]
     h_out = torch.empty((1, 3) + tuple(N_FINE[::-1]), dtype=torch.complex128, pin_memory=True)
     e2e = []
-    for k in range(args.steps):
+    for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -240,51 +252,68 @@ def run_ours(args, rank, world, local_rank):
         e2e.append(time.perf_counter() - t0)
         ok = ok and r["status"] == "OK"
 
-    # per-kernel durations (CUDA events on the solver's stream) on the finest grid
-    prob.set_initial(si.gaussian_guess(N_FINE, L_BOX, si.seed_for(2, rank), vortex=True)[None], level=0)
-    prof = prob.profile(iters=10, precision=prec, tol=TOL)
+    # per-kernel durations (CUDA events on the solver's stream) on every level's grid
+    last = results[-1]
+    prof = {}
+    for lev in range(LEVELS):
+        n = tuple(k >> (LEVELS - 1 - lev) for k in N_FINE)
+        with Problem(n, L_BOX, [PAR]) as pl:
+            pl.set_initial(si.gaussian_guess(n, L_BOX, si.seed_for(2, rank), vortex=True)[None], level=0)
+            prof[n[0]] = pl.profile(iters=20, precision=prec, tol=TOL)
     fp64_peak, fp32_peak = probe_peaks()
     prob.close()
-
     if rank != 0:
         return None
-    iters = results[-1]
-    total_it = sum(ms for _, ms in prof)
-    dom_name, dom_ms = max(prof, key=lambda kv: kv[1])
-    flops = kernel_flops(dom_name)
-    achieved = flops / (dom_ms * 1e-3) / 1e12
-    ms_per_step = max_total_ms / args.steps
-    value = world * 1000.0 / ms_per_step
+
+    # dominant (kernel, level): largest share of the solve time = iterations x duration
+    elem = 8 if prec == 1 else 16
+    shares = {}
+    for lev, its in enumerate(last["level_iters"]):
+        n = N_FINE[0] >> (LEVELS - 1 - lev)
+        for name, ms in prof[n]:
+            shares[(name, n)] = shares.get((name, n), 0.0) + its * ms
+    total_share = sum(shares.values())
+    (dom_name, dom_n), _ = max(shares.items(), key=lambda kv: kv[1])
+    dom_ms = statistics.mean([ms for name, ms in prof[dom_n] if name == dom_name])
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm_peak = None
-    if os.path.exists(peaks_file):
-        hbm_peak = json.load(open(peaks_file)).get("hbm_gbs")
+    hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else 6800.0
+    if prec == 1:
+        by = kernel_bytes(dom_name, (dom_n, dom_n), elem)
+        achieved = by / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{dom_name} @ {dom_n}^2 (FP32)", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes_per_launch": by}
+    else:
+        fl = kernel_flops(dom_name, (dom_n, dom_n))
+        achieved = fl / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": f"{dom_name} @ {dom_n}^2 (FP64)", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA-chain probe gpsoc_probe_peaks, this run (of measured)",
+                "algorithmic_flops_per_launch": fl}
+    roof.update({"ms_per_launch": dom_ms, "share_of_solve": shares[(dom_name, dom_n)] / total_share})
+    ms_per_step = max_total_ms / args.steps
     out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "metric": METRIC, "value": world * 1000.0 / ms_per_step, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
+        "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "solves_per_step_per_gpu": 1,
                    "grid": "512x512", "levels": [128, 256, 512], "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp64_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak > 0 else None,
-                     "traffic": None, "peak_source": "FP64 FMA-chain probe (gpsoc_probe_peaks), this run",
-                     "share_of_iteration": dom_ms / total_it, "ms_per_launch": dom_ms,
-                     "algorithmic_flops_per_launch": flops},
-        "kernels_ms_per_iteration_512": {k: round(v, 5) for k, v in prof},
-        "solve": {"status_ok": ok, "energy": iters["energy"], "mu": iters["mu"], "iters_finest": iters["iters"],
-                  "iters_total": iters["total_iters"], "level_iters": iters["level_iters"],
-                  "beta_resets": iters["beta_resets"],
-                  "halvings": iters["halvings"]},
-        "e2e": {"value": 1.0 / statistics.mean(e2e), "unit": "solves/s",
+        "fp64_plain": fp64,
+        "roofline": roof,
+        "kernels_us_per_iteration": {str(n): {k: round(v * 1e3, 2) for k, v in pr} for n, pr in prof.items()},
+        "solve": {"status_ok": ok, "energy": last["energy"], "mu": last["mu"], "iters_total": last["total_iters"],
+                  "level_iters": last["level_iters"], "fp32_iters": last["fp32_iters"],
+                  "fp64_iters": last["fp64_iters"], "beta_resets": last["beta_resets"]},
+        "e2e": {"value": world / statistics.mean(e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h_in.numpy().nbytes), "d2h_bytes_per_step": int(h_out.numpy().nbytes)},
-        "gpu_launches": int(launches),
+        "gpu_launches": launches_timed,
         "clocks": clk.summary(),
         "peaks": {"fp64_tflops_probe": fp64_peak, "fp32_tflops_probe": fp32_peak, "hbm_gbs_measured": hbm_peak},
     }
-    return out, results[-1]
+    return out, last
 
 
 def per_level_iters(res_dict, n_levels):
@@ -295,10 +324,12 @@ def per_level_iters(res_dict, n_levels):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed solves of the plain FP64 comparison")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     args = ap.parse_args()
     if args.warmup < 3:

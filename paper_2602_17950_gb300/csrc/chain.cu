@@ -18,14 +18,70 @@
 // second array G = F_y^{-1}[v_y F_y A] and multiplied by x after the x inverse.
 #include "gpsoc_internal.cuh"
 #include "scalar.cuh"
+#include "fft.cuh"
 
 namespace gpsoc {
 
-static constexpr int kThreads = 256;
+static constexpr int kThreads = 384;
+// reduction scratch (doubles) behind the tiles: block_reduce needs 16 per warp + 16
+static constexpr int kRedDoubles = 16 * (kThreads / 32) + 16;
 
 template <class T>
 __device__ __forceinline__ void load_tw(cx_t<T>* s_tw, const cx_t<T>* tw, int n) {
-  for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) s_tw[k] = tw[k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[k] = tw[k];
+}
+
+// Row tiles: nlines lines of padded length NP; thread -> (line q, group g0), E
+// elements per thread.  NI = 2 transforms the same line of buf0 and buf1 together.
+template <class C, bool INV, int NI, int E>
+__device__ __forceinline__ void row_fft_e(C* buf0, C* buf1, int nlines, int NP, int L, const C* tw) {
+  const int G = (1 << L) / E;
+  const int q = threadIdx.x / G, g0 = threadIdx.x - q * G;
+  const bool act = q < nlines;
+  const int qq = act ? q : 0;
+  if constexpr (NI == 2) {
+    C* const l2[2] = {buf0 + qq * NP, buf1 + qq * NP};
+    const bool a2[2] = {act, act};
+    stockham_fft<C, INV, E, 2>(l2, a2, g0, 1, L, tw);
+  } else {
+    C* const l1[1] = {buf0 + qq * NP};
+    const bool a1[1] = {act};
+    stockham_fft<C, INV, E, 1>(l1, a1, g0, 1, L, tw);
+  }
+}
+
+template <class C, bool INV, int NI>
+__device__ __forceinline__ void row_fft(C* buf0, C* buf1, int nlines, int NP, int L, const C* tw, int ept) {
+  if (ept == 8) row_fft_e<C, INV, NI, 8>(buf0, buf1, nlines, NP, L, tw);
+  else if (ept == 4) row_fft_e<C, INV, NI, 4>(buf0, buf1, nlines, NP, L, tw);
+  else row_fft_e<C, INV, NI, 2>(buf0, buf1, nlines, NP, L, tw);
+}
+
+// Column tiles: three components (stride CS) of TC columns, element stride TC.
+// ni3: a thread takes one (column, group) for all three components; otherwise
+// one (component, column, group).  E elements per thread.
+template <class C, bool INV, int E>
+__device__ __forceinline__ void col_fft_e(C* base, int CS, int TC, int L, const C* tw, int ni3) {
+  if (ni3) {
+    const int t = threadIdx.x % TC, g0 = threadIdx.x / TC;
+    C* const l3[3] = {base + t, base + CS + t, base + 2 * CS + t};
+    const bool a3[3] = {true, true, true};
+    stockham_fft<C, INV, E, 3>(l3, a3, g0, TC, L, tw);
+  } else {
+    const int nl = 3 * TC;
+    const int line = threadIdx.x % nl, g0 = threadIdx.x / nl;
+    const int c = line / TC, t = line - c * TC;
+    C* const l1[1] = {base + c * CS + t};
+    const bool a1[1] = {true};
+    stockham_fft<C, INV, E, 1>(l1, a1, g0, TC, L, tw);
+  }
+}
+
+template <class C, bool INV>
+__device__ __forceinline__ void col_fft(C* base, int CS, int TC, int L, const C* tw, int ept, int ni3) {
+  if (ept == 8) col_fft_e<C, INV, 8>(base, CS, TC, L, tw, ni3);
+  else if (ept == 4) col_fft_e<C, INV, 4>(base, CS, TC, L, tw, ni3);
+  else col_fft_e<C, INV, 2>(base, CS, TC, L, tw, ni3);
 }
 
 // spin terms shared by the pointwise epilogues (working precision W):
@@ -59,7 +115,7 @@ __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&sl
 // Working precision W = T: FP64 kernels compute in double, FP32 kernels in float
 // (per-thread partial sums in T, block and grid reductions in FP64).
 template <class T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
+__global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept) {
   using C = cx_t<T>;
   using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -72,11 +128,12 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   const int rb = blockIdx.x % bps;
   if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   C* s_tw = (C*)smem_raw;
-  C* buf0 = s_tw + (nx >> 1);
+  C* buf0 = s_tw + nx;
   const int per = R * nx;             // elements of one component in the tile
+  const int NP = fft_padded_len(nx), CP = R * NP;   // padded line length, component stride in smem
   constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
-  C* buf1 = buf0 + 3 * per;
-  double* red = (double*)(buf1 + (two ? 3 * per : 0));
+  C* buf1 = buf0 + 3 * CP;
+  double* red = (double*)(buf1 + (two ? 3 * CP : 0));
   load_tw<T>(s_tw, A.tw[0], nx);
   const long long sbase = (long long)s * 3 * npts;
   const long long rbase = (long long)rb * R * nx;   // offset of the tile inside a component
@@ -96,10 +153,10 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const long long off = rbase + e;
-      const int pos = r * nx + bitrev(j, Lx);
+      const int pos = r * NP + fft_pad(j);
       if (MODE == ROW_FWD_PLAIN) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) buf0[c * per + pos] = A.in0[sbase + c * npts + off];
+        for (int c = 0; c < 3; ++c) buf0[c * CP + pos] = A.in0[sbase + c * npts + off];
       } else if (MODE == ROW_FWD_UPD) {
         // the step accepted by the previous iteration: Phi <- (cos t Phi + sin t P/|P|)/norm
         // (Eqs. formula-pcg, update); reduce max |dPhi|^2 for the stop1 test
@@ -114,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
             A.out1[sbase + c * npts + off] = o;
             f = o;
           }
-          buf0[c * per + pos] = f;
+          buf0[c * CP + pos] = f;
         }
       } else if (MODE == ROW_FWD_PROJ) {
         // D = -z + beta P_prev, P = D - Re<D, Phi> Phi (Eq. formula-project); reduce ||P||^2
@@ -129,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
           p.y = di - cproj * f.y;
           A.out1[sbase + c * npts + off] = p;
           acc[0] += p.x * p.x + p.y * p.y;
-          buf0[c * per + pos] = p;
+          buf0[c * CP + pos] = p;
         }
       } else {  // ROW_FWD_PRE: r = H Phi - mu Phi, then P_V^{1/2} r (Eq. PreCondPot)
         C f[3], h[3];
@@ -152,15 +209,16 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
           W den = al[c] + V + c0 * rho;
           den = fmax(den, (W)1e-12 * al[c]);
           const W sc = rsqrt_w<W>(den);
-          buf0[c * per + pos] = mk<C>(rr.x * sc, rr.y * sc);
+          buf0[c * CP + pos] = mk<C>(rr.x * sc, rr.y * sc);
         }
       }
     }
     __syncthreads();
-    fft_dit<C, false>(buf0, Lx, 3 * R, 3 * R, 0, nx, 1, s_tw, false);
+    row_fft<C, false, 1>(buf0, buf1, 3 * R, NP, Lx, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int pos = (e / nx) * NP + fft_pad(e % nx);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + rbase + e] = buf0[c * per + e];
+      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + rbase + e] = buf0[c * CP + pos];
     }
     if (MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE || (MODE == ROW_FWD_UPD && upd)) {
       const bool mx[1] = {MODE != ROW_FWD_PROJ};
@@ -172,16 +230,18 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   }
 
   // ---------------------------------------------------------------- inverse passes
-  // load natural order, DIF inverse -> bit-reversed positions in shared memory
+  // natural order in shared memory, inverse transform in place
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
+    const int pos = (e / nx) * NP + fft_pad(e % nx);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      buf0[c * per + e] = A.in0[sbase + c * npts + rbase + e];
-      if (two) buf1[c * per + e] = A.in1[sbase + c * npts + rbase + e];
+      buf0[c * CP + pos] = A.in0[sbase + c * npts + rbase + e];
+      if (two) buf1[c * CP + pos] = A.in1[sbase + c * npts + rbase + e];
     }
   }
   __syncthreads();
-  fft_dif<C, false>(buf0, Lx, two ? 6 * R : 3 * R, two ? 6 * R : 3 * R, 0, nx, 1, s_tw, true);
+  if (two) row_fft<C, true, 2>(buf0, buf1, 3 * R, NP, Lx, s_tw, ept);
+  else row_fft<C, true, 1>(buf0, buf1, 3 * R, NP, Lx, s_tw, ept);
 
   const W inv_n = (W)1 / (W)npts;
   const W Om = (W)ph.Omega;
@@ -189,10 +249,10 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
-      const int pos = r * nx + bitrev(j, Lx);
+      const int pos = r * NP + fft_pad(j);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const C v = buf0[c * per + pos];
+        const C v = buf0[c * CP + pos];
         A.out0[sbase + c * npts + rbase + e] = mk<C>(v.x * sc, v.y * sc);
       }
     }
@@ -206,7 +266,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
     const W c0 = (W)ph.c0;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
-      const int pos = r * nx + bitrev(j, Lx);
+      const int pos = r * NP + fft_pad(j);
       const long long off = rbase + e;
       W rho = (W)0;
 #pragma unroll
@@ -221,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
         W den = al[c] + V + c0 * rho;
         den = fmax(den, (W)1e-12 * al[c]);
         const W sc = inv_n * rsqrt_w<W>(den);
-        const C v = buf0[c * per + pos];
+        const C v = buf0[c * CP + pos];
         const C z = mk<C>(v.x * sc, v.y * sc);
         A.out0[sbase + c * npts + off] = z;
         const C rr = A.in2[sbase + c * npts + off];
@@ -246,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
   for (int k = 0; k < 13; ++k) acc[k] = (W)0;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int r = e / nx, j = e - r * nx;
-    const int pos = r * nx + bitrev(j, Lx);
+    const int pos = r * NP + fft_pad(j);
     const long long off = rbase + e;
     const long long row = off / nx;
     const int iy = (int)(row % ny), iz = (int)(row / ny);
@@ -257,8 +317,8 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       u[c] = A.in2[sbase + c * npts + off];
-      const C t = buf0[c * per + pos];
-      const C gg = buf1[c * per + pos];
+      const C t = buf0[c * CP + pos];
+      const C gg = buf1[c * CP + pos];
       lin_r[c] = (t.x - Om * x * gg.x) * inv_n + V * u[c].x;
       lin_i[c] = (t.y - Om * x * gg.y) * inv_n + V * u[c].y;
     }
@@ -360,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R) {
 // Tile: inner indices [i0, i0 + TC) of the axis-`axis` lines at outer index o.
 // Shared layout of one component: [axis position][TC].
 template <class T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC) {
+__global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC, int ept, int ni3) {
   using C = cx_t<T>;
   using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -376,10 +436,11 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const int o = tb / tpo;
   const int i0 = (tb % tpo) * TC;
   C* s_tw = (C*)smem_raw;
-  C* buf = s_tw + (na >> 1);
+  C* buf = s_tw + na;
   const int per = na * TC;
-  C* buf2 = buf + 3 * per;            // second 3-component buffer (YINV_H) or 1-component temp (YMID_H)
-  double* red = (double*)(buf2 + 3 * per);
+  const int CS = fft_padded_len(na) * TC;   // component stride in smem: [row (padded)][TC]
+  C* buf2 = buf + 3 * CS;            // second 3-component buffer (YINV_H) or 1-component temp (YMID_H)
+  double* red = (double*)(buf2 + 3 * CS);
   load_tw<T>(s_tw, A.tw[axis], na);
   const long long sbase = (long long)s * 3 * npts;
   const long long obase = (long long)o * na * ni + i0;
@@ -388,42 +449,35 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const double piA = A.g.piL[axis];
   const int nx = A.g.n[0];
 
-  // load in0 tile: bit-reversed positions for forward (DIT) modes, natural for inverse (DIF)
-  const bool fwd_first = (MODE != COL_INV && MODE != COL_YINV_H);
+  // load the in0 tile (and in1 for YINV_H) in natural order
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    const int pj = fwd_first ? bitrev(j, La) : j;
+    const int ix = fft_pad(j) * TC + t;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) buf[c * per + pj * TC + t] = A.in0[sbase + c * npts + obase + (long long)j * ni + t];
-  }
-  if (MODE == COL_YINV_H) {
-    for (int e = threadIdx.x; e < per; e += blockDim.x) {
-      const int j = e / TC, t = e - j * TC;
-      const int pj = bitrev(j, La);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) buf2[c * per + pj * TC + t] = A.in1[sbase + c * npts + obase + (long long)j * ni + t];
+    for (int c = 0; c < 3; ++c) {
+      buf[c * CS + ix] = A.in0[sbase + c * npts + obase + (long long)j * ni + t];
+      if (MODE == COL_YINV_H) buf2[c * CS + ix] = A.in1[sbase + c * npts + obase + (long long)j * ni + t];
     }
   }
   __syncthreads();
 
   if (MODE == COL_FWD) {
-    fft_dit<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, false);
+    col_fft<C, false>(buf, CS, TC, La, s_tw, ept, ni3);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + obase + (long long)j * ni + t] = buf[c * per + j * TC + t];
+      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + obase + (long long)j * ni + t] = buf[c * CS + fft_pad(j) * TC + t];
     }
     return;
   }
   if (MODE == COL_INV) {
-    fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
+    col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
-      const int pj = bitrev(j, La);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const C v = buf[c * per + pj * TC + t];
+        const C v = buf[c * CS + fft_pad(j) * TC + t];
         A.out0[sbase + c * npts + obase + (long long)j * ni + t] = mk<C>(v.x * sc, v.y * sc);
       }
     }
@@ -440,20 +494,22 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   if (MODE == COL_YINV_H) {
     // buf: C (natural) -> DIF inverse -> bit-reversed F_y^-1 C
     // buf2: A (bit-reversed) -> DIT forward -> natural F_y A; multiply by v_y; DIF inverse -> G
-    fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
-    fft_dit<C, true>(buf2, La, 3 * TC, TC, per, 1, TC, s_tw, false);
+    col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
+    col_fft<C, false>(buf2, CS, TC, La, s_tw, ept, ni3);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
-      const W vy = wavenum<W>(e / TC, na, piA);
+      const int j = e / TC, t = e - j * TC;
+      const W vy = wavenum<W>(j, na, piA);
+      const int ix = fft_pad(j) * TC + t;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf2[c * per + e] = cscale(buf2[c * per + e], vy);
+      for (int c = 0; c < 3; ++c) buf2[c * CS + ix] = cscale(buf2[c * CS + ix], vy);
     }
     __syncthreads();
-    fft_dif<C, true>(buf2, La, 3 * TC, TC, per, 1, TC, s_tw, true);
+    col_fft<C, true>(buf2, CS, TC, La, s_tw, ept, ni3);
     const W nfac = (W)A.g.n[1] * (W)A.g.n[2];  // ny * nz
     const W nz = (W)A.g.n[2];
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
-      const int pj = bitrev(j, La);
+      const int ix = fft_pad(j) * TC + t;
       W kx, ky;
       kinner(t, kx, ky);
       const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
@@ -462,9 +518,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const C a = A.in1[gi + c * npts];
-        const C cv = buf[c * per + pj * TC + t];
+        const C cv = buf[c * CS + ix];
         A.out0[gi + c * npts] = mk<C>(cv.x + rot * a.x, cv.y + rot * a.y);
-        const C gv = buf2[c * per + pj * TC + t];
+        const C gv = buf2[c * CS + ix];
         A.out1[gi + c * npts] = mk<C>(gv.x * nz, gv.y * nz);
       }
     }
@@ -472,19 +528,24 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   }
 
   // forward transform along the axis: natural-order spectrum in buf
-  fft_dit<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, false);
+  col_fft<C, false>(buf, CS, TC, La, s_tw, ept, ni3);
 
   if (MODE == COL_YMID_H) {
-    // G_c = F_y^-1[v_y F_y A_c], one component at a time through buf2 (1 component)
-    for (int c = 0; c < 3; ++c) {
-      for (int e = threadIdx.x; e < per; e += blockDim.x) buf2[e] = cscale(buf[c * per + e], wavenum<W>(e / TC, na, piA));
-      __syncthreads();
-      fft_dif<C, true>(buf2, La, TC, TC, 0, 1, TC, s_tw, true);
-      for (int e = threadIdx.x; e < per; e += blockDim.x) {
-        const int j = e / TC, t = e - j * TC;
-        A.out1[sbase + c * npts + obase + (long long)j * ni + t] = buf2[bitrev(j, La) * TC + t];
-      }
-      __syncthreads();
+    // G_c = F_y^-1[v_y F_y A_c] for the three components at once (buf2)
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / TC, t = e - j * TC;
+      const int ix = fft_pad(j) * TC + t;
+      const W vy = wavenum<W>(j, na, piA);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) buf2[c * CS + ix] = cscale(buf[c * CS + ix], vy);
+    }
+    __syncthreads();
+    col_fft<C, true>(buf2, CS, TC, La, s_tw, ept, ni3);
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / TC, t = e - j * TC;
+      const int ix = fft_pad(j) * TC + t;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.out1[sbase + c * npts + obase + (long long)j * ni + t] = buf2[c * CS + ix];
     }
   }
 
@@ -494,6 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const W g = (W)ph.gamma;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
+    const int ix = fft_pad(j) * TC + t;
     W kx, ky, kz = (W)0;
     kinner(t, kx, ky);
     if (axis == 1) ky = wavenum<W>(j, na, piA);
@@ -501,9 +563,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     const W k2h = (W)0.5 * (kx * kx + ky * ky + kz * kz);
     if (MODE == COL_MID_PRE) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf[c * per + e] = cscale(buf[c * per + e], (W)1 / (al[c] + k2h));
+      for (int c = 0; c < 3; ++c) buf[c * CS + ix] = cscale(buf[c * CS + ix], (W)1 / (al[c] + k2h));
     } else {
-      const C p1 = buf[e], p0 = buf[per + e], pm = buf[2 * per + e];
+      const C p1 = buf[ix], p0 = buf[CS + ix], pm = buf[2 * CS + ix];
       // kinetic per component (Parseval): sum 1/2 |k|^2 |phat_l|^2
       acc[0] += k2h * (p1.x * p1.x + p1.y * p1.y);
       acc[1] += k2h * (p0.x * p0.x + p0.y * p0.y);
@@ -515,19 +577,19 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       const W b_r = s1r * p1.x - s1i * p1.y, b_i = s1r * p1.y + s1i * p1.x;   // s1 p1
       const W c_r = s0r * pm.x - s0i * pm.y, c_i = s0r * pm.y + s0i * pm.x;   // s0 pm
       const W d_r = s1r * p0.x - s1i * p0.y, d_i = s1r * p0.y + s1i * p0.x;   // s1 p0
-      buf[e] = mk<C>(k2h * p1.x - g * a_r, k2h * p1.y - g * a_i);
-      buf[per + e] = mk<C>(k2h * p0.x - g * (b_r + c_r), k2h * p0.y - g * (b_i + c_i));
-      buf[2 * per + e] = mk<C>(k2h * pm.x - g * d_r, k2h * pm.y - g * d_i);
+      buf[ix] = mk<C>(k2h * p1.x - g * a_r, k2h * p1.y - g * a_i);
+      buf[CS + ix] = mk<C>(k2h * p0.x - g * (b_r + c_r), k2h * p0.y - g * (b_i + c_i));
+      buf[2 * CS + ix] = mk<C>(k2h * pm.x - g * d_r, k2h * pm.y - g * d_i);
     }
   }
   __syncthreads();
-  fft_dif<C, true>(buf, La, 3 * TC, TC, per, 1, TC, s_tw, true);
+  col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
 
   const W nrot = (W)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
   const W Om = (W)ph.Omega;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    const int pj = bitrev(j, La);
+    const int ix = fft_pad(j) * TC + t;
     const long long gi = sbase + obase + (long long)j * ni + t;
     if (MODE == COL_YMID_H) {
       W kx, ky;
@@ -537,12 +599,12 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const C a = A.in0[gi + c * npts];
-        const C v = buf[c * per + pj * TC + t];
+        const C v = buf[c * CS + ix];
         A.out0[gi + c * npts] = mk<C>(v.x + rot * a.x, v.y + rot * a.y);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out0[gi + c * npts] = buf[c * per + pj * TC + t];
+      for (int c = 0; c < 3; ++c) A.out0[gi + c * npts] = buf[c * CS + ix];
     }
   }
   if (MODE == COL_MID_H || MODE == COL_YMID_H) {
@@ -572,7 +634,7 @@ int col_tc(const Geo& g, int axis) {
   const int na = g.n[axis];
   const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
   const int no = (int)(g.npts / ((long long)na * ni));
-  const int tmin = (sizeof(T) == 8) ? 2 : 4;            // >= one 32-byte sector per line segment
+  const int tmin = (sizeof(T) == 8) ? 1 : 4;            // FP32: >= one 32-byte sector per line segment
   const int target = (sizeof(T) == 8) ? 1024 : 2048;    // elements of one component per tile
   int tc = target / na;
   if (tc < 1) tc = 1;
@@ -581,11 +643,26 @@ int col_tc(const Geo& g, int axis) {
   return tc;
 }
 
-static int threads_for(int per) {
-  int t = (3 * per) / 2;   // butterflies per stage of the three components
-  if (t > 256) t = 256;
+// elements per thread of the FFT passes: 8 (radix-8 passes) unless the tile
+// would then have fewer than 128 threads, in which case 4 or 2 (more threads,
+// more passes); and the matching thread count (multiple of 32, >= 64)
+static int pick_ept(int work /* complex elements of the three components */) {
+  int e = 8;
+  while (e > 2 && work / e < 128) e >>= 1;
+  return e;
+}
+static int round_threads(int t) {
   if (t < 64) t = 64;
   return (t + 31) & ~31;
+}
+
+template <class T>
+static void col_cfg(const Geo& g, int axis, int& tc, int& ept, int& ni3, int& threads) {
+  tc = col_tc<T>(g, axis);
+  const int work = tc * g.n[axis];
+  ni3 = (sizeof(T) == 4 && work >= 2048) ? 1 : 0;
+  if (ni3) { ept = 8; threads = round_threads(work / 8); }
+  else { ept = pick_ept(3 * work); threads = round_threads(3 * work / ept); }
 }
 
 template <class T>
@@ -607,14 +684,16 @@ static size_t row_smem(const Geo& g, int mode) {
   const int R = row_rows_per_block<T>(g);
   const int per = R * g.n[0];
   const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
-  return sizeof(C) * ((g.n[0] >> 1) + 3 * per * (two ? 2 : 1)) + 160 * sizeof(double);
+  (void)per;
+  const int CP = R * fft_padded_len(g.n[0]);
+  return sizeof(C) * (g.n[0] + 3 * CP * (two ? 2 : 1)) + kRedDoubles * sizeof(double);
 }
 
 template <class T>
 static size_t col_smem(const Geo& g, int axis) {
   using C = cx_t<T>;
-  const int per = g.n[axis] * col_tc<T>(g, axis);
-  return sizeof(C) * ((g.n[axis] >> 1) + 6 * per) + 160 * sizeof(double);
+  const int CS = fft_padded_len(g.n[axis]) * col_tc<T>(g, axis);
+  return sizeof(C) * (g.n[axis] + 6 * CS) + kRedDoubles * sizeof(double);
 }
 
 template <class T, int MODE>
@@ -622,7 +701,8 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int R = row_rows_per_block<T>(a.g);
   const int nb = row_blocks_per_solve<T>(a.g, Launch{}) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE);
-  k_row<T, MODE><<<nb, threads_for(R * a.g.n[0]), sm, st>>>(a, R);
+  const int ept = pick_ept(3 * R * a.g.n[0]);
+  k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
 }
 
 template <class T>
@@ -642,10 +722,11 @@ void launch_row(int mode, const ChainArgs<T>& a, int, const Launch&, cudaStream_
 
 template <class T, int MODE>
 static void col_go(int axis, const ChainArgs<T>& a, cudaStream_t st) {
-  const int tc = col_tc<T>(a.g, axis);
+  int tc, ept, ni3, threads;
+  col_cfg<T>(a.g, axis, tc, ept, ni3, threads);
   const int nb = col_blocks_per_solve<T>(a.g, axis, Launch{}) * a.nsolve;
   const size_t sm = col_smem<T>(a.g, axis);
-  k_col<T, MODE><<<nb, threads_for(tc * a.g.n[axis]), sm, st>>>(a, axis, tc);
+  k_col<T, MODE><<<nb, threads, sm, st>>>(a, axis, tc, ept, ni3);
 }
 
 template <class T>

@@ -190,15 +190,27 @@ TrapDev make_trap(const gpsoc_problem* p, int level) {
 gpsoc_status twiddles(gpsoc_problem* p, int n, const double2** out) {
   auto it = p->tw64.find(n);
   if (it != p->tw64.end()) { *out = it->second; return GPSOC_OK; }
-  std::vector<double2> h(n / 2);
+  // W_n^k = exp(-2 pi i k / n), k < n; from the first octant by symmetry so that
+  // W^(n/4) = -i, W^(n/2) = -1 hold exactly
+  std::vector<double2> h(n);
   const double PI = 3.14159265358979323846;
-  for (int k = 0; k < n / 2; ++k) {
-    const double ang = -2.0 * PI * (double)k / (double)n;
-    h[k] = make_double2(std::cos(ang), std::sin(ang));
+  for (int k = 0; k < n; ++k) {
+    int m = k;
+    double sc = 1.0, ss = 1.0;
+    // reduce to [0, n/4]: W^(k) = -i W^(k - n/4)
+    int quad = 0;
+    while (m > n / 4) { m -= n / 4; ++quad; }
+    double c, sn;
+    if (2 * m <= n / 4) { const double a = 2.0 * PI * m / n; c = std::cos(a); sn = std::sin(a); }
+    else { const double a = 2.0 * PI * (n / 4 - m) / n; c = std::sin(a); sn = std::cos(a); }
+    (void)sc; (void)ss;
+    double re = c, im = -sn;   // exp(-i a)
+    for (int q = 0; q < quad; ++q) { const double t = re; re = im; im = -t; }   // multiply by -i
+    h[k] = make_double2(re, im);
   }
   double2* d = nullptr;
-  CK(cudaMalloc(&d, sizeof(double2) * (n / 2 > 0 ? n / 2 : 1)));
-  CK(cudaMemcpy(d, h.data(), sizeof(double2) * (n / 2), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&d, sizeof(double2) * n));
+  CK(cudaMemcpy(d, h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
   p->tw64[n] = d;
   *out = d;
   return GPSOC_OK;
@@ -210,13 +222,13 @@ gpsoc_status twiddles(gpsoc_problem* p, int n, const float2** out) {
   const double2* d64;
   gpsoc_status s = twiddles(p, n, &d64);
   if (s != GPSOC_OK) return s;
-  std::vector<double2> h(n / 2);
-  CK(cudaMemcpy(h.data(), d64, sizeof(double2) * (n / 2), cudaMemcpyDeviceToHost));
-  std::vector<float2> f(n / 2);
-  for (int k = 0; k < n / 2; ++k) f[k] = make_float2((float)h[k].x, (float)h[k].y);
+  std::vector<double2> h(n);
+  CK(cudaMemcpy(h.data(), d64, sizeof(double2) * n, cudaMemcpyDeviceToHost));
+  std::vector<float2> f(n);
+  for (int k = 0; k < n; ++k) f[k] = make_float2((float)h[k].x, (float)h[k].y);
   float2* d = nullptr;
-  CK(cudaMalloc(&d, sizeof(float2) * (n / 2 > 0 ? n / 2 : 1)));
-  CK(cudaMemcpy(d, f.data(), sizeof(float2) * (n / 2), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&d, sizeof(float2) * n));
+  CK(cudaMemcpy(d, f.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
   p->tw32[n] = d;
   *out = d;
   return GPSOC_OK;

@@ -258,68 +258,6 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, co
   for (int k = 0; k < K; ++k) v[k] = res[k];
 }
 
-// ------------------------------------------------------------------ shared-memory FFT
-// Radix-2 FFTs of nseq sequences of length 2^L held in shared memory.  Element e
-// of sequence q is at buf[(q / qgroup) * gstride + (q % qgroup) * qstride + e * estride].
-// tw[k] = exp(-2 pi i k / 2^L), k < 2^(L-1); inverse = conjugate twiddles (no 1/n).
-// fft_dit: bit-reversed input -> natural output (decimation in time).
-// fft_dif: natural input -> bit-reversed output (decimation in frequency).
-// SEQ_FAST: consecutive threads take consecutive sequences (column tiles)
-// instead of consecutive butterflies of one sequence (rows).
-template <class C, bool SEQ_FAST>
-__device__ __forceinline__ void fft_dit(C* buf, int L, int nseq, int qgroup, int gstride, int qstride,
-                                        int estride, const C* tw, bool inverse) {
-  const int half = 1 << (L - 1);
-  const int total = nseq * half;
-  for (int st = 0; st < L; ++st) {
-    const int m = 1 << st;
-    const int tws = L - 1 - st;  // twiddle index = pos << tws
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-      int q, j;
-      if (SEQ_FAST) { q = b % nseq; j = b / nseq; }
-      else { q = b >> (L - 1); j = b & (half - 1); }
-      const int pos = j & (m - 1);
-      const int i0 = ((j >> st) << (st + 1)) + pos;
-      C* base = buf + (q / qgroup) * gstride + (q % qgroup) * qstride;
-      C w = tw[pos << tws];
-      if (inverse) w.y = -w.y;
-      C u = base[i0 * estride];
-      C t = cmul(w, base[(i0 + m) * estride]);
-      base[i0 * estride] = cadd(u, t);
-      base[(i0 + m) * estride] = csub(u, t);
-    }
-    __syncthreads();
-  }
-}
-
-template <class C, bool SEQ_FAST>
-__device__ __forceinline__ void fft_dif(C* buf, int L, int nseq, int qgroup, int gstride, int qstride,
-                                        int estride, const C* tw, bool inverse) {
-  const int half = 1 << (L - 1);
-  const int total = nseq * half;
-  for (int st = L - 1; st >= 0; --st) {
-    const int m = 1 << st;
-    const int tws = L - 1 - st;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-      int q, j;
-      if (SEQ_FAST) { q = b % nseq; j = b / nseq; }
-      else { q = b >> (L - 1); j = b & (half - 1); }
-      const int pos = j & (m - 1);
-      const int i0 = ((j >> st) << (st + 1)) + pos;
-      C* base = buf + (q / qgroup) * gstride + (q % qgroup) * qstride;
-      C w = tw[pos << tws];
-      if (inverse) w.y = -w.y;
-      C u = base[i0 * estride];
-      C v = base[(i0 + m) * estride];
-      base[i0 * estride] = cadd(u, v);
-      base[(i0 + m) * estride] = cmul(csub(u, v), w);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ int bitrev(int j, int L) { return (int)(__brev((unsigned)j) >> (32 - L)); }
-
 // ------------------------------------------------------------------ host-side launch helpers
 struct Launch {
   int rows_per_block;   // row passes

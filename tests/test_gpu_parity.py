@@ -317,3 +317,33 @@ def test_mixed_precision_cm_batch_matches_fp64():
         assert r32["energy"] == pytest.approx(r64["energy"], rel=1e-10)
         assert r32["mu"] == pytest.approx(r64["mu"], rel=1e-10)
         assert np.max(np.abs(np.abs(out[1][1][k]) ** 2 - np.abs(out[0][1][k]) ** 2)) < 1e-8
+
+
+@pytest.mark.parametrize("n,L", [((512, 512), (16.0, 16.0)), ((1024, 16), (20.0, 4.0)), ((16, 1024), (4.0, 20.0))])
+def test_apply_h_large_tiles_match_oracle(n, L):
+    # the largest tiles (384-thread blocks, radix-8 passes) in FP64
+    psi = si.smooth_random_state(n, L, 51, width=min(L) / 3)[None]
+    with Problem(n, L, [PAR]) as p:
+        p.set_initial(psi)
+        hp, obs = p.apply_h()
+        phi = p.psi()[0]
+    m = oracle_model(n, L, PAR)
+    assert rel_max(hp[0], m.H(phi)) < 1e-11
+    assert obs[0, 0] == pytest.approx(m.energy(phi), rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [64, 256, 512])
+def test_fp32_iteration_kernels_run_at_every_tile_shape(n):
+    # every kernel of the FP32 and FP64 iterations, at the tile shapes of each grid:
+    # the profiled iterations run, the energy decreases and stays finite
+    L = (16.0, 16.0)
+    psi = si.gaussian_guess((n, n), L, 61, vortex=True)[None]
+    with Problem((n, n), L, [(0.9, 1.0, 1000.0, -5.0)]) as p:
+        for prec in (1, 0):
+            p.set_initial(psi)
+            E0 = p.observables()[0][0]
+            prof = p.profile(iters=6, precision=prec)
+            assert len(prof) == 10 and all(ms > 0 for _, ms in prof)
+            E1, _, m = p.observables()
+            assert np.isfinite(E1[0]) and E1[0] < E0
+            assert abs(m[0].sum() - 1.0) < 1e-6
