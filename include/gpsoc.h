@@ -224,6 +224,33 @@ uint64_t gpsoc_kernel_launches(const gpsoc_problem* p);
  * independent FMA chains run for a few milliseconds.  Either pointer may be NULL. */
 gpsoc_status gpsoc_probe_peaks(double* fp64_tflops, double* fp32_tflops);
 
+/* Allocation-free H(Phi) (no counterpart in the paper).  For callers that must
+ * not allocate device memory when they need the Hamiltonian -- a framework that
+ * owns all device memory through its own pool, a real-time loop that cannot
+ * afford (or synchronise on) cudaMalloc/cudaFree, code held to a memory budget
+ * reserved up front.  Computes what gpsoc_apply_h computes, H_l(Phi) of
+ * Eqs. eigen1-eigen3 and the 9 observables per solve, without a problem object:
+ *   grid, trap (HARMONIC or HARMONIC_QUARTIC), params[batch]: as gpsoc_create;
+ *   d_psi:  device, batch * 3 * npts complex128, [solve][component][z][y][x],
+ *           used as given (not normalised), read only;
+ *   d_hpsi: device, same layout, receives H_l(Phi);
+ *   obs:    host, 9 doubles per solve as gpsoc_apply_h (may be NULL);
+ *   cuda_stream: cudaStream_t or NULL (legacy default stream); the call
+ *           returns after the stream has finished its work.
+ * It allocates nothing: intermediate arrays, partial sums, twiddle tables and
+ * per-solve scalars live in one fixed 16 MiB array in device memory, present on
+ * every GPU that loads the library until the process exits.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and sets
+ * kernel attributes; make that first call before any stream capture.  Problems
+ * whose working set (about 4 x batch x 3 x npts x 16 bytes plus small tables)
+ * exceeds the array return GPSOC_EBUDGET.  Failures are reported by the
+ * returned status only (gpsoc_last_error is not updated: that would allocate a
+ * message).  All calls share the one array: calls
+ * whose work overlaps on the GPU (other threads, other streams) race and must
+ * be serialised by the caller. */
+gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpsoc_trap* trap, const gpsoc_params* params,
+                                   int batch, const void* d_psi, void* d_hpsi, double* obs, void* cuda_stream);
+
 /* Message describing the last failure on this thread ("" if none). */
 const char* gpsoc_last_error(void);
 

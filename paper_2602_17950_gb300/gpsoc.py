@@ -87,6 +87,8 @@ _PROTOS = {
     "gpsoc_profile_name": (C.c_char_p, [C.c_void_p, C.c_int]),
     "gpsoc_kernel_launches": (C.c_uint64, [C.c_void_p]),
     "gpsoc_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "gpsoc_apply_h_noalloc": (C.c_int, [C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "gpsoc_last_error": (C.c_char_p, []),
     "gpsoc_version": (C.c_char_p, []),
 }
@@ -131,6 +133,27 @@ def probe_peaks():
     a, b = C.c_double(0), C.c_double(0)
     _check(library().gpsoc_probe_peaks(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def apply_h_noalloc(n, L, params, trap, d_psi: int, d_hpsi: int, stream="torch") -> np.ndarray:
+    """H(Phi) of the device states at d_psi into d_hpsi without any device
+    allocation (gpsoc_apply_h_noalloc); returns the 9 observables per solve.
+    For callers that cannot allocate device memory at this point."""
+    dim = len(n)
+    g = Grid(dim, (C.c_int * 3)(*(list(n) + [1] * (3 - dim))), (C.c_double * 3)(*(list(L) + [1.0] * (3 - dim))))
+    trap = dict(trap or {})
+    gv = list(trap.get("g", (1.0, 1.0, 1.0))) + [1.0] * 3
+    t = Trap(int(trap.get("kind", 0)), (C.c_double * 3)(*gv[:3]), float(trap.get("quad", 0.0)),
+             float(trap.get("quart", 0.0)), None)
+    params = [tuple(p) for p in params]
+    parr = (Params * len(params))(*[Params(*map(float, p)) for p in params])
+    obs = np.zeros((len(params), 9))
+    st = _current_stream() if stream == "torch" else stream
+    code = library().gpsoc_apply_h_noalloc(C.byref(g), C.byref(t), parr, len(params), C.c_void_p(d_psi),
+                                           C.c_void_p(d_hpsi), _ptr(obs), st)
+    if code != 0:   # this entry point reports through its status only
+        raise GpsocError(code, "gpsoc_apply_h_noalloc failed")
+    return obs
 
 
 class Problem:
