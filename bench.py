@@ -168,6 +168,25 @@ def oracle_sample(iters_per_level, budget_s: float = 20.0):
                    f"counts of one solve {list(iters_per_level)}")
 
 
+# ------------------------------------------------------------------ multi-rank bookkeeping
+def reduce_max(value: float) -> float:
+    """Maximum of `value` over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return value
+    dev = "cpu" if tdist.get_backend() == "gloo" else torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, max_total_ms: float, solves_per_step: int = 1) -> float:
+    """Solves per second of the whole job: every rank solves `solves_per_step`
+    independent problems per step; the job takes the slowest rank's time."""
+    return world * solves_per_step * steps * 1000.0 / max_total_ms
+
+
 # ------------------------------------------------------------------ our arm
 def timed_solves(prob, opts, d_psi0, flush, stream, warmup, steps, torch):
     """W untimed + K timed solves from the device-resident guess; CUDA events on
@@ -218,11 +237,9 @@ def run_ours(args, rank, world, local_rank):
         lat, results = timed_solves(prob, opts, d_psi0, flush, stream, args.warmup, args.steps, torch)
     launches = prob.kernel_launches() - launches0
     torch.cuda.synchronize()
-    t = torch.tensor([sum(lat)], dtype=torch.float64, device=dev)
     if dist:
         tdist.barrier()
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    max_total_ms = float(t.item())
+    max_total_ms = reduce_max(sum(lat))
     ok = all(r["status"] == "OK" for r in results)
     # warm-up launches are included in the counter: keep only the timed solves' share
     launches_timed = int(round(launches * args.steps / (args.steps + args.warmup)))
@@ -293,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
     roof.update({"ms_per_launch": dom_ms, "share_of_solve": shares[(dom_name, dom_n)] / total_share})
     ms_per_step = max_total_ms / args.steps
     out = {
-        "metric": METRIC, "value": world * 1000.0 / ms_per_step, "unit": "solves/s", "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(world, args.steps, max_total_ms), "unit": "solves/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -316,6 +334,62 @@ def run_ours(args, rank, world, local_rank):
     return out, last
 
 
+def batch_case(args):
+    """The batched sweep: `batch` solves of 256^2 on [-12,12]^2 with parameters drawn
+    Omega~U[0,0.95], gamma~U[0,2], beta0~U[100,2000], beta1~U[-10,10] and seeded
+    Gaussian / vortex guesses, solved together in one problem (every PCG iteration
+    one graph replay for all live solves), FP64 and mixed precision, same tolerance."""
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    build()
+    n, L = (256, 256), (12.0, 12.0)
+    B = args.batch
+    pars = [(q.Omega, q.gamma, q.beta0, q.beta1) for q in si.batch_params(si.seed_for(3, 0), B)]
+    psi = np.stack([si.gaussian_guess(n, L, si.seed_for(3, k), vortex=bool(k % 2)) for k in range(B)])
+    out = {"workload": f"{B} solves of 256x256 on [-12,12]^2, random parameters, stop |dE|<1e-12",
+           "max_iter": args.max_iter}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        with Problem(n, L, pars) as p:
+            p.set_initial(psi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = p.solve(tol=TOL, precision=prec, max_iter=args.max_iter, check_every=64)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        ok = sum(r["status"] == "OK" for r in res)
+        its = [r["total_iters"] for r in res]
+        out[name] = {"seconds": dt, "solves_per_s": B / dt, "converged": ok,
+                     "iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)),
+                     "energies": [round(r["energy"], 10) for r in res[:4]]}
+    print(json.dumps(out))
+
+
+def kernel_case(args):
+    """Per-kernel durations of PCG iterations of `batch` solves on an N x N grid of
+    the bench workload (box, trap, parameters), CUDA events on the solver's stream.
+    A small, bounded command for kernel-level profiling."""
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    build()
+    n = (args.kernel_case, args.kernel_case)
+    prec = 1 if args.precision == "mixed" else 0
+    psi = np.stack([si.gaussian_guess(n, L_BOX, si.seed_for(2, k), vortex=True) for k in range(args.batch)])
+    with Problem(n, L_BOX, [PAR] * args.batch) as p:
+        p.set_initial(psi)
+        p.profile(iters=args.warmup, precision=prec, tol=TOL)
+        prof = p.profile(iters=max(args.steps, 1) * 10, precision=prec, tol=TOL)
+    elem = 8 if prec == 1 else 16
+    out = {"kernel_case": f"{n[0]}x{n[1]} x {args.batch} solves", "precision": args.precision,
+           "us_per_launch": {k: round(v * 1e3, 2) for k, v in prof},
+           "iteration_us": round(sum(v for _, v in prof) * 1e3, 2),
+           "gbs_per_launch": {k: round(kernel_bytes(k, n, elem) * args.batch / (v * 1e-3) / 1e9, 1)
+                              for k, v in prof if kernel_bytes(k, n, elem) > 0}}
+    torch.cuda.synchronize()
+    print(json.dumps(out))
+
+
 def per_level_iters(res_dict, n_levels):
     """Iterations of one solve on each multigrid level (coarsest first)."""
     return [int(v) for v in res_dict["level_iters"][:n_levels]]
@@ -331,7 +405,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed solves of the plain FP64 comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--kernel-case", type=int, default=0, metavar="N",
+                    help="only time the kernels of PCG iterations on N x N grids (per-kernel CUDA events)")
+    ap.add_argument("--batch", type=int, default=1, help="solves per problem in --kernel-case / --batch-case")
+    ap.add_argument("--batch-case", action="store_true", help="the batched random-parameter sweep at 256^2")
+    ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of --batch-case")
     args = ap.parse_args()
+    if args.batch_case:
+        batch_case(args)
+        return
+    if args.kernel_case:
+        kernel_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

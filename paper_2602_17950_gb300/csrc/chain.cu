@@ -57,32 +57,9 @@ __device__ __forceinline__ void row_fft(C* buf0, C* buf1, int nlines, int NP, in
   else row_fft_e<C, INV, NI, 2>(buf0, buf1, nlines, NP, L, tw);
 }
 
-// Column tiles: three components (stride CS) of TC columns, element stride TC.
-// ni3: a thread takes one (column, group) for all three components; otherwise
-// one (component, column, group).  E elements per thread.
-template <class C, bool INV, int E>
-__device__ __forceinline__ void col_fft_e(C* base, int CS, int TC, int L, const C* tw, int ni3) {
-  if (ni3) {
-    const int t = threadIdx.x % TC, g0 = threadIdx.x / TC;
-    C* const l3[3] = {base + t, base + CS + t, base + 2 * CS + t};
-    const bool a3[3] = {true, true, true};
-    stockham_fft<C, INV, E, 3>(l3, a3, g0, TC, L, tw);
-  } else {
-    const int nl = 3 * TC;
-    const int line = threadIdx.x % nl, g0 = threadIdx.x / nl;
-    const int c = line / TC, t = line - c * TC;
-    C* const l1[1] = {base + c * CS + t};
-    const bool a1[1] = {true};
-    stockham_fft<C, INV, E, 1>(l1, a1, g0, TC, L, tw);
-  }
-}
-
-template <class C, bool INV>
-__device__ __forceinline__ void col_fft(C* base, int CS, int TC, int L, const C* tw, int ept, int ni3) {
-  if (ept == 8) col_fft_e<C, INV, 8>(base, CS, TC, L, tw, ni3);
-  else if (ept == 4) col_fft_e<C, INV, 4>(base, CS, TC, L, tw, ni3);
-  else col_fft_e<C, INV, 2>(base, CS, TC, L, tw, ni3);
-}
+// odd padded length of a column line in shared memory (distinct banks for
+// consecutive columns)
+__host__ __device__ __forceinline__ int col_line_len(int n) { return fft_padded_len(n) | 1; }
 
 // spin terms shared by the pointwise epilogues (working precision W):
 //   a = conj(p0) p1 + conj(pm) p0  so that F_-/sqrt2 = a, F_+/sqrt2 = conj(a),
@@ -417,10 +394,13 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
 }
 
 // ============================================================== column passes (y or z axis)
-// Tile: inner indices [i0, i0 + TC) of the axis-`axis` lines at outer index o.
-// Shared layout of one component: [axis position][TC].
+// Tile: inner indices [i0, i0 + TC) of the axis-`axis` lines at outer index o, all
+// three components.  Shared memory holds every (component, column) line
+// contiguously, line (c, t) at (c TC + t) NPL with an odd padded length NPL, so
+// the transforms run exactly as in the row passes and the transposing accesses
+// (consecutive threads on consecutive columns) fall on distinct banks.
 template <class T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC, int ept, int ni3) {
+__global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC, int ept) {
   using C = cx_t<T>;
   using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -438,8 +418,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   C* s_tw = (C*)smem_raw;
   C* buf = s_tw + na;
   const int per = na * TC;
-  const int CS = fft_padded_len(na) * TC;   // component stride in smem: [row (padded)][TC]
-  C* buf2 = buf + 3 * CS;            // second 3-component buffer (YINV_H) or 1-component temp (YMID_H)
+  const int NPL = col_line_len(na);            // odd padded line length
+  const int CS = TC * NPL;                     // component stride in smem
+  C* buf2 = buf + 3 * CS;            // second 3-component tile (YMID_H, YINV_H)
   double* red = (double*)(buf2 + 3 * CS);
   load_tw<T>(s_tw, A.tw[axis], na);
   const long long sbase = (long long)s * 3 * npts;
@@ -448,36 +429,37 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const PhysDev ph = A.phys[s];
   const double piA = A.g.piL[axis];
   const int nx = A.g.n[0];
+  // smem index of element j of column t, component c: c * CS + t * NPL + pad(j)
+  auto sidx = [&](int c, int t, int j) { return c * CS + t * NPL + fft_pad(j); };
 
-  // load the in0 tile (and in1 for YINV_H) in natural order
+  // load the in0 tile (and in1 for YINV_H) in natural order; global reads coalesced over t
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    const int ix = fft_pad(j) * TC + t;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      buf[c * CS + ix] = A.in0[sbase + c * npts + obase + (long long)j * ni + t];
-      if (MODE == COL_YINV_H) buf2[c * CS + ix] = A.in1[sbase + c * npts + obase + (long long)j * ni + t];
+      buf[sidx(c, t, j)] = A.in0[sbase + c * npts + obase + (long long)j * ni + t];
+      if (MODE == COL_YINV_H) buf2[sidx(c, t, j)] = A.in1[sbase + c * npts + obase + (long long)j * ni + t];
     }
   }
   __syncthreads();
 
   if (MODE == COL_FWD) {
-    col_fft<C, false>(buf, CS, TC, La, s_tw, ept, ni3);
+    row_fft<C, false, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + obase + (long long)j * ni + t] = buf[c * CS + fft_pad(j) * TC + t];
+      for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + obase + (long long)j * ni + t] = buf[sidx(c, t, j)];
     }
     return;
   }
   if (MODE == COL_INV) {
-    col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
+    row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const C v = buf[c * CS + fft_pad(j) * TC + t];
+        const C v = buf[sidx(c, t, j)];
         A.out0[sbase + c * npts + obase + (long long)j * ni + t] = mk<C>(v.x * sc, v.y * sc);
       }
     }
@@ -492,24 +474,21 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   };
 
   if (MODE == COL_YINV_H) {
-    // buf: C (natural) -> DIF inverse -> bit-reversed F_y^-1 C
-    // buf2: A (bit-reversed) -> DIT forward -> natural F_y A; multiply by v_y; DIF inverse -> G
-    col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
-    col_fft<C, false>(buf2, CS, TC, La, s_tw, ept, ni3);
+    // buf: C -> F_y^-1 C;  buf2: A -> F_y A, times v_y, F_y^-1 -> G
+    row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, false, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
       const W vy = wavenum<W>(j, na, piA);
-      const int ix = fft_pad(j) * TC + t;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf2[c * CS + ix] = cscale(buf2[c * CS + ix], vy);
+      for (int c = 0; c < 3; ++c) buf2[sidx(c, t, j)] = cscale(buf2[sidx(c, t, j)], vy);
     }
     __syncthreads();
-    col_fft<C, true>(buf2, CS, TC, La, s_tw, ept, ni3);
+    row_fft<C, true, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     const W nfac = (W)A.g.n[1] * (W)A.g.n[2];  // ny * nz
     const W nz = (W)A.g.n[2];
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
-      const int ix = fft_pad(j) * TC + t;
       W kx, ky;
       kinner(t, kx, ky);
       const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
@@ -518,9 +497,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const C a = A.in1[gi + c * npts];
-        const C cv = buf[c * CS + ix];
+        const C cv = buf[sidx(c, t, j)];
         A.out0[gi + c * npts] = mk<C>(cv.x + rot * a.x, cv.y + rot * a.y);
-        const C gv = buf2[c * CS + ix];
+        const C gv = buf2[sidx(c, t, j)];
         A.out1[gi + c * npts] = mk<C>(gv.x * nz, gv.y * nz);
       }
     }
@@ -528,24 +507,22 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   }
 
   // forward transform along the axis: natural-order spectrum in buf
-  col_fft<C, false>(buf, CS, TC, La, s_tw, ept, ni3);
+  row_fft<C, false, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
 
   if (MODE == COL_YMID_H) {
     // G_c = F_y^-1[v_y F_y A_c] for the three components at once (buf2)
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
-      const int ix = fft_pad(j) * TC + t;
       const W vy = wavenum<W>(j, na, piA);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) buf2[c * CS + ix] = cscale(buf[c * CS + ix], vy);
+      for (int c = 0; c < 3; ++c) buf2[sidx(c, t, j)] = cscale(buf[sidx(c, t, j)], vy);
     }
     __syncthreads();
-    col_fft<C, true>(buf2, CS, TC, La, s_tw, ept, ni3);
+    row_fft<C, true, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
-      const int ix = fft_pad(j) * TC + t;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out1[sbase + c * npts + obase + (long long)j * ni + t] = buf2[c * CS + ix];
+      for (int c = 0; c < 3; ++c) A.out1[sbase + c * npts + obase + (long long)j * ni + t] = buf2[sidx(c, t, j)];
     }
   }
 
@@ -555,17 +532,18 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const W g = (W)ph.gamma;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    const int ix = fft_pad(j) * TC + t;
+    const int i1 = sidx(0, t, j), i2 = sidx(1, t, j), i3 = sidx(2, t, j);
     W kx, ky, kz = (W)0;
     kinner(t, kx, ky);
     if (axis == 1) ky = wavenum<W>(j, na, piA);
     else kz = wavenum<W>(j, na, piA);
     const W k2h = (W)0.5 * (kx * kx + ky * ky + kz * kz);
     if (MODE == COL_MID_PRE) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) buf[c * CS + ix] = cscale(buf[c * CS + ix], (W)1 / (al[c] + k2h));
+      buf[i1] = cscale(buf[i1], (W)1 / (al[0] + k2h));
+      buf[i2] = cscale(buf[i2], (W)1 / (al[1] + k2h));
+      buf[i3] = cscale(buf[i3], (W)1 / (al[2] + k2h));
     } else {
-      const C p1 = buf[ix], p0 = buf[CS + ix], pm = buf[2 * CS + ix];
+      const C p1 = buf[i1], p0 = buf[i2], pm = buf[i3];
       // kinetic per component (Parseval): sum 1/2 |k|^2 |phat_l|^2
       acc[0] += k2h * (p1.x * p1.x + p1.y * p1.y);
       acc[1] += k2h * (p0.x * p0.x + p0.y * p0.y);
@@ -577,19 +555,18 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       const W b_r = s1r * p1.x - s1i * p1.y, b_i = s1r * p1.y + s1i * p1.x;   // s1 p1
       const W c_r = s0r * pm.x - s0i * pm.y, c_i = s0r * pm.y + s0i * pm.x;   // s0 pm
       const W d_r = s1r * p0.x - s1i * p0.y, d_i = s1r * p0.y + s1i * p0.x;   // s1 p0
-      buf[ix] = mk<C>(k2h * p1.x - g * a_r, k2h * p1.y - g * a_i);
-      buf[CS + ix] = mk<C>(k2h * p0.x - g * (b_r + c_r), k2h * p0.y - g * (b_i + c_i));
-      buf[2 * CS + ix] = mk<C>(k2h * pm.x - g * d_r, k2h * pm.y - g * d_i);
+      buf[i1] = mk<C>(k2h * p1.x - g * a_r, k2h * p1.y - g * a_i);
+      buf[i2] = mk<C>(k2h * p0.x - g * (b_r + c_r), k2h * p0.y - g * (b_i + c_i));
+      buf[i3] = mk<C>(k2h * pm.x - g * d_r, k2h * pm.y - g * d_i);
     }
   }
   __syncthreads();
-  col_fft<C, true>(buf, CS, TC, La, s_tw, ept, ni3);
+  row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
 
   const W nrot = (W)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
   const W Om = (W)ph.Omega;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
-    const int ix = fft_pad(j) * TC + t;
     const long long gi = sbase + obase + (long long)j * ni + t;
     if (MODE == COL_YMID_H) {
       W kx, ky;
@@ -599,12 +576,12 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const C a = A.in0[gi + c * npts];
-        const C v = buf[c * CS + ix];
+        const C v = buf[sidx(c, t, j)];
         A.out0[gi + c * npts] = mk<C>(v.x + rot * a.x, v.y + rot * a.y);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out0[gi + c * npts] = buf[c * CS + ix];
+      for (int c = 0; c < 3; ++c) A.out0[gi + c * npts] = buf[sidx(c, t, j)];
     }
   }
   if (MODE == COL_MID_H || MODE == COL_YMID_H) {
@@ -615,31 +592,32 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 }
 
 // ============================================================== launch helpers
-// Tile shapes depend on the grid only (never on the batch), so a solve reduces
-// in the same order alone and inside a batch.  Small grids get small tiles so
-// that one solve still spreads over many SMs.
+// Tile shapes: the largest tile (up to 512 elements per row tile, 1024 per
+// column tile and component) that still gives the launch at least kTargetBlocks
+// blocks over all solves, so small grids and single solves spread over the SMs
+// while large batches keep long coalesced line segments.
+static constexpr int kTargetBlocks = 304;   // two blocks per SM of a 152-SM GB300
+
 template <class T>
-int row_rows_per_block(const Geo& g) {
+int row_rows_per_block(const Geo& g, int nsolve) {
   const int nx = g.n[0];
   const int rows = (int)(g.npts / nx);
   int R = 512 / nx;
   if (R < 1) R = 1;
-  while (R > 1 && rows / R < 256) R >>= 1;
   if (R > rows) R = rows;
+  while (R > 1 && (long long)nsolve * (rows / R) < kTargetBlocks) R >>= 1;
   return R;
 }
 
 template <class T>
-int col_tc(const Geo& g, int axis) {
+int col_tc(const Geo& g, int axis, int nsolve) {
   const int na = g.n[axis];
   const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
   const int no = (int)(g.npts / ((long long)na * ni));
-  const int tmin = (sizeof(T) == 8) ? 1 : 4;            // FP32: >= one 32-byte sector per line segment
-  const int target = (sizeof(T) == 8) ? 1024 : 2048;    // elements of one component per tile
-  int tc = target / na;
+  int tc = 1024 / na;
   if (tc < 1) tc = 1;
-  while (tc > tmin && (ni / tc) * no < 256) tc >>= 1;
   if (tc > ni) tc = ni;
+  while (tc > 1 && (long long)nsolve * (ni / tc) * no < kTargetBlocks) tc >>= 1;
   return tc;
 }
 
@@ -657,31 +635,30 @@ static int round_threads(int t) {
 }
 
 template <class T>
-static void col_cfg(const Geo& g, int axis, int& tc, int& ept, int& ni3, int& threads) {
-  tc = col_tc<T>(g, axis);
-  const int work = tc * g.n[axis];
-  ni3 = (sizeof(T) == 4 && work >= 2048) ? 1 : 0;
-  if (ni3) { ept = 8; threads = round_threads(work / 8); }
-  else { ept = pick_ept(3 * work); threads = round_threads(3 * work / ept); }
+static void col_cfg(const Geo& g, int axis, int nsolve, int& tc, int& ept, int& threads) {
+  tc = col_tc<T>(g, axis, nsolve);
+  const int work = 3 * tc * g.n[axis];
+  ept = pick_ept(work);
+  threads = round_threads(work / ept);
 }
 
 template <class T>
-int row_blocks_per_solve(const Geo& g, const Launch&) {
-  return (int)(g.npts / g.n[0]) / row_rows_per_block<T>(g);
+int row_blocks_per_solve(const Geo& g, int nsolve) {
+  return (int)(g.npts / g.n[0]) / row_rows_per_block<T>(g, nsolve);
 }
 
 template <class T>
-int col_blocks_per_solve(const Geo& g, int axis, const Launch&) {
+int col_blocks_per_solve(const Geo& g, int axis, int nsolve) {
   const int na = g.n[axis];
   const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
   const int no = (int)(g.npts / ((long long)na * ni));
-  return (ni / col_tc<T>(g, axis)) * no;
+  return (ni / col_tc<T>(g, axis, nsolve)) * no;
 }
 
 template <class T>
-static size_t row_smem(const Geo& g, int mode) {
+static size_t row_smem(const Geo& g, int mode, int nsolve) {
   using C = cx_t<T>;
-  const int R = row_rows_per_block<T>(g);
+  const int R = row_rows_per_block<T>(g, nsolve);
   const int per = R * g.n[0];
   const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
   (void)per;
@@ -690,17 +667,17 @@ static size_t row_smem(const Geo& g, int mode) {
 }
 
 template <class T>
-static size_t col_smem(const Geo& g, int axis) {
+static size_t col_smem(const Geo& g, int axis, int nsolve) {
   using C = cx_t<T>;
-  const int CS = fft_padded_len(g.n[axis]) * col_tc<T>(g, axis);
+  const int CS = col_line_len(g.n[axis]) * col_tc<T>(g, axis, nsolve);
   return sizeof(C) * (g.n[axis] + 6 * CS) + kRedDoubles * sizeof(double);
 }
 
 template <class T, int MODE>
 static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
-  const int R = row_rows_per_block<T>(a.g);
-  const int nb = row_blocks_per_solve<T>(a.g, Launch{}) * a.nsolve;
-  const size_t sm = row_smem<T>(a.g, MODE);
+  const int R = row_rows_per_block<T>(a.g, a.nsolve);
+  const int nb = row_blocks_per_solve<T>(a.g, a.nsolve) * a.nsolve;
+  const size_t sm = row_smem<T>(a.g, MODE, a.nsolve);
   const int ept = pick_ept(3 * R * a.g.n[0]);
   k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
 }
@@ -722,11 +699,11 @@ void launch_row(int mode, const ChainArgs<T>& a, int, const Launch&, cudaStream_
 
 template <class T, int MODE>
 static void col_go(int axis, const ChainArgs<T>& a, cudaStream_t st) {
-  int tc, ept, ni3, threads;
-  col_cfg<T>(a.g, axis, tc, ept, ni3, threads);
-  const int nb = col_blocks_per_solve<T>(a.g, axis, Launch{}) * a.nsolve;
-  const size_t sm = col_smem<T>(a.g, axis);
-  k_col<T, MODE><<<nb, threads, sm, st>>>(a, axis, tc, ept, ni3);
+  int tc, ept, threads;
+  col_cfg<T>(a.g, axis, a.nsolve, tc, ept, threads);
+  const int nb = col_blocks_per_solve<T>(a.g, axis, a.nsolve) * a.nsolve;
+  const size_t sm = col_smem<T>(a.g, axis, a.nsolve);
+  k_col<T, MODE><<<nb, threads, sm, st>>>(a, axis, tc, ept);
 }
 
 template <class T>
@@ -760,10 +737,10 @@ template void launch_row<double>(int, const ChainArgs<double>&, int, const Launc
 template void launch_row<float>(int, const ChainArgs<float>&, int, const Launch&, cudaStream_t);
 template void launch_col<double>(int, int, const ChainArgs<double>&, const Launch&, cudaStream_t);
 template void launch_col<float>(int, int, const ChainArgs<float>&, const Launch&, cudaStream_t);
-template int row_blocks_per_solve<double>(const Geo&, const Launch&);
-template int row_blocks_per_solve<float>(const Geo&, const Launch&);
-template int col_blocks_per_solve<double>(const Geo&, int, const Launch&);
-template int col_blocks_per_solve<float>(const Geo&, int, const Launch&);
+template int row_blocks_per_solve<double>(const Geo&, int);
+template int row_blocks_per_solve<float>(const Geo&, int);
+template int col_blocks_per_solve<double>(const Geo&, int, int);
+template int col_blocks_per_solve<float>(const Geo&, int, int);
 template cudaError_t chain_prepare<double>();
 template cudaError_t chain_prepare<float>();
 

@@ -269,9 +269,8 @@ ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   s.phys = p->d_phys;
   s.part = p->d_part;
   s.pmax = p->pmax;
-  Launch lc{};
-  s.nb_row = row_blocks_per_solve<T>(g, lc);
-  s.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, lc);
+  s.nb_row = row_blocks_per_solve<T>(g, p->batch);
+  s.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, p->batch);
   s.nsolve = p->batch;
   s.phase = phase;
   s.npts = g.npts;
@@ -288,8 +287,8 @@ ScalarCtx scalar_ctx(gpsoc_problem* p, const Geo& g, const OptsDev& o, int flags
   c.phys = p->d_phys;
   c.part = p->d_part;
   c.pmax = p->pmax;
-  c.nb_row = row_blocks_per_solve<T>(g, Launch{});
-  c.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, Launch{});
+  c.nb_row = row_blocks_per_solve<T>(g, p->batch);
+  c.nb_col = col_blocks_per_solve<T>(g, p->dim - 1, p->batch);
   c.npts = g.npts;
   c.dV = g.dV;
   c.opts = o;
@@ -304,7 +303,7 @@ ElemArgs<T> elem_args(gpsoc_problem* p, const Geo& g, int gate) {
   e.part = p->d_part;
   e.pmax = p->pmax;
   e.npts = g.npts;
-  e.bps = row_blocks_per_solve<double>(g, Launch{});
+  e.bps = row_blocks_per_solve<double>(g, p->batch);
   e.nsolve = p->batch;
   e.gate = gate;
   e.scalev = p->d_scale;
@@ -708,14 +707,9 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
     if (cudaMalloc(sl, arr) != cudaSuccess) { cudaGetLastError(); return bail(GPSOC_ENOMEM, "device allocation failed"); }
   }
   // partial-sum stride: the largest blocks-per-solve of any pass at the finest level
-  Launch lc{};
-  p->pmax = 1;
-  for (int lev = 0; lev <= p->max_level; ++lev) {
-    const Geo gl = make_geo(p, lev);
-    p->pmax = std::max(p->pmax, std::max(row_blocks_per_solve<double>(gl, lc), row_blocks_per_solve<float>(gl, lc)));
-    for (int ax = 1; ax < p->dim; ++ax)
-      p->pmax = std::max(p->pmax, std::max(col_blocks_per_solve<double>(gl, ax, lc), col_blocks_per_solve<float>(gl, ax, lc)));
-  }
+  // the most blocks any pass can use per solve: one row, or one column line, per block
+  p->pmax = (int)(g.npts / g.n[0]);
+  for (int ax = 1; ax < p->dim; ++ax) p->pmax = std::max(p->pmax, (int)(g.npts / g.n[ax]));
   if (cudaMalloc(&p->d_part, sizeof(double) * (size_t)batch * NSLOT * p->pmax) != cudaSuccess)
     return bail(GPSOC_ENOMEM, "device allocation failed");
   if (cudaMalloc(&p->d_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");

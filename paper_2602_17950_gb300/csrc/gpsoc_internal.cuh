@@ -23,7 +23,9 @@ template <> struct Cx<double> { using type = double2; };
 template <> struct Cx<float> { using type = float2; };
 template <class T> using cx_t = typename Cx<T>::type;
 
-template <class C> __host__ __device__ __forceinline__ C mk(double re, double im) {
+// build a complex of the array type from values of any real type (no detour
+// through double: conversions run on the scarce FP64 pipe)
+template <class C, class A, class B> __host__ __device__ __forceinline__ C mk(A re, B im) {
   C c; c.x = (decltype(c.x))re; c.y = (decltype(c.y))im; return c;
 }
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
@@ -197,13 +199,14 @@ __device__ __forceinline__ W trap_value(const TrapDev& t, const Geo& g, int ix, 
 // ------------------------------------------------------------------ block reductions (deterministic)
 // FP64 block reductions in a fixed order.  FP64 issue slots are scarce on this
 // part (about 1/64 of FP32), so a multi-value reduction does not run one
-// shuffle tree per value (5 adds per lane per value): a warp first performs a
-// reduce-scatter over 16 value slots -- at each of four halving steps a lane
-// keeps one half of its values and adds the partner lane's copy of that half --
-// so that every lane ends with one slot (16 adds per lane in total), then the
-// two half-warps are added, and the warps are added in index order.
-// scratch: >= 16 * (blockDim.x / 32) + 16 doubles.  Every thread receives the
-// K results in v.  is_max is honoured for K == 1 only (multi-value calls sum).
+// shuffle tree per value (5 adds per lane per value).  With KP = K rounded up to
+// a power of two, a warp first performs a reduce-scatter over the KP value slots
+// -- at each halving step a lane keeps one half of its values and adds the
+// partner lane's copy of that half -- so that every lane holds one slot
+// (KP - 1 adds), then the 32/KP lanes holding the same slot are added in a
+// fixed butterfly (log2(32/KP) adds), and the warps are added in index order.
+// scratch: >= 16 * (blockDim.x / 32) + 16 doubles.  Every thread receives the K
+// results in v.  is_max is honoured for K == 1 only (multi-value calls sum).
 template <int K>
 __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, const bool (&is_max)[K]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -227,13 +230,15 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, co
     return;
   }
   static_assert(K <= 16, "block_reduce handles at most 16 values");
-  double x[16];
+  constexpr int KP = (K <= 2) ? 2 : (K <= 4) ? 4 : (K <= 8) ? 8 : 16;
+  constexpr int LB = (KP == 2) ? 1 : (KP == 4) ? 2 : (KP == 8) ? 3 : 4;
+  double x[KP];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) x[k] = (k < K) ? v[k] : 0.0;
-  // reduce-scatter: after the step with offset ofs each lane holds hv/2 slots
+  for (int k = 0; k < KP; ++k) x[k] = (k < K) ? v[k] : 0.0;
+  // reduce-scatter over the low LB lane bits
 #pragma unroll
-  for (int st = 0; st < 4; ++st) {
-    const int ofs = 1 << st, half = 8 >> st;
+  for (int st = 0; st < LB; ++st) {
+    const int ofs = 1 << st, half = (KP / 2) >> st;
     const bool up = (lane & ofs) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
@@ -242,10 +247,14 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, co
       x[i] = keep + __shfl_xor_sync(0xffffffffu, send, ofs);
     }
   }
-  x[0] += __shfl_xor_sync(0xffffffffu, x[0], 16);
-  // lane l (< 16) now holds slot 8 b0 + 4 b1 + 2 b2 + b3 of its bits b0..b3
-  const int slot = ((lane & 1) << 3) | ((lane & 2) << 1) | ((lane & 4) >> 1) | ((lane & 8) >> 3);
-  if (lane < 16) scratch[warp * 16 + slot] = x[0];
+  // lanes equal in the low LB bits hold the same slot: add them
+#pragma unroll
+  for (int ofs = KP; ofs < 32; ofs <<= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], ofs);
+  // slot of lane l: its low LB bits reversed (bit 0 chose the highest half first)
+  int slot = 0;
+#pragma unroll
+  for (int b = 0; b < LB; ++b) slot |= ((lane >> b) & 1) << (LB - 1 - b);
+  if (lane < KP) scratch[warp * 16 + slot] = x[0];
   __syncthreads();
   double* res = scratch + 16 * nw;
   if (threadIdx.x < K) {
@@ -293,10 +302,11 @@ template <class T>
 void launch_row(int mode, const ChainArgs<T>& a, int nblocks_total, const Launch& lc, cudaStream_t s);
 template <class T>
 void launch_col(int mode, int axis, const ChainArgs<T>& a, const Launch& lc, cudaStream_t s);
+// blocks per solve of the row passes / column passes for a launch over nsolve solves
 template <class T>
-int row_blocks_per_solve(const Geo& g, const Launch& lc);
+int row_blocks_per_solve(const Geo& g, int nsolve);
 template <class T>
-int col_blocks_per_solve(const Geo& g, int axis, const Launch& lc);
+int col_blocks_per_solve(const Geo& g, int axis, int nsolve);
 template <class T>
 cudaError_t chain_prepare();   // sets max dynamic shared memory attributes
 

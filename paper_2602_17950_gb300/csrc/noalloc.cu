@@ -110,9 +110,9 @@ extern "C" gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpso
   }
   // scratch layout: A, B, W, G arrays | partial sums | states | parameters | twiddles | observables
   const size_t arr = sizeof(double2) * (size_t)batch * 3 * g.npts;
-  const int nb_row = row_blocks_per_solve<double>(g, Launch{});
+  const int nb_row = row_blocks_per_solve<double>(g, batch);
   int pmax = nb_row;
-  for (int ax = 1; ax < g.d; ++ax) pmax = std::max(pmax, col_blocks_per_solve<double>(g, ax, Launch{}));
+  for (int ax = 1; ax < g.d; ++ax) pmax = std::max(pmax, col_blocks_per_solve<double>(g, ax, batch));
   size_t off = 0;
   const size_t o_arr = off; off += align256(4 * arr);
   const size_t o_part = off; off += align256(sizeof(double) * (size_t)batch * NSLOT * pmax);
@@ -203,7 +203,7 @@ extern "C" gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpso
   ScalarArgs x{};
   x.st = sst; x.phys = ph; x.part = part; x.pmax = pmax;
   x.nb_row = nb_row;
-  x.nb_col = col_blocks_per_solve<double>(g, g.d - 1, Launch{});
+  x.nb_col = col_blocks_per_solve<double>(g, g.d - 1, batch);
   x.nsolve = batch; x.phase = PH_OBS; x.npts = g.npts; x.dV = g.dV; x.force = 1;
   launch_scalar(x, st);
   k_gather_obs<<<(batch + 127) / 128, 128, 0, st>>>(sst, batch, dobs);

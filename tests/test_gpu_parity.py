@@ -223,22 +223,26 @@ def test_cascadic_multigrid_matches_oracle():
 
 
 def test_batch_results_equal_single_solves():
-    # each solve of a batch gives bitwise the result it gives alone
+    # each solve of a batch gives the result it gives alone, within the parity tolerances
+    # (tile shapes follow the total work, so the summation order may differ);
+    # anisotropic trap: the minimisers are unique up to the global phase
     n, L = (32, 32), (6.0, 6.0)
+    trap = {"kind": 0, "g": (1.0, 1.1)}
     pars = [(0.2, 0.4, 50.0, -2.0), (0.7, 1.1, 120.0, 3.0), (0.0, 0.0, 10.0, 0.0)]
     psis = np.stack([si.gaussian_guess(n, L, 200 + k) for k in range(3)])
-    with Problem(n, L, pars) as p:
+    with Problem(n, L, pars, trap=trap) as p:
         p.set_initial(psis)
-        rb = p.solve(tol=1e-12)
+        rb = p.solve(tol=1e-12, res_tol=1e-9)
         gb = p.psi()
     for k in range(3):
-        with Problem(n, L, [pars[k]]) as p:
+        with Problem(n, L, [pars[k]], trap=trap) as p:
             p.set_initial(psis[k][None])
-            r1 = p.solve(tol=1e-12)[0]
+            r1 = p.solve(tol=1e-12, res_tol=1e-9)[0]
             g1 = p.psi()[0]
-        assert rb[k]["iters"] == r1["iters"]
-        assert rb[k]["energy"] == r1["energy"]
-        assert np.array_equal(gb[k], g1)
+        assert rb[k]["status"] == "OK" and r1["status"] == "OK"
+        assert rb[k]["energy"] == pytest.approx(r1["energy"], rel=1e-10)
+        assert rb[k]["mu"] == pytest.approx(r1["mu"], rel=1e-10)
+        assert np.max(np.abs(np.abs(gb[k]) ** 2 - np.abs(g1) ** 2)) < 1e-8
 
 
 def test_status_codes():
