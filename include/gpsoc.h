@@ -94,8 +94,9 @@ typedef struct {
  *   check_every  iterations run between host convergence checks (0 = 16).
  *   fp32_switch  GPSOC_MIXED only: the FP32 phase of each level ends when an
  *                accepted step changes the energy by less than
- *                tol + fp32_switch * |E| (or when no decrease is found);
- *                0 selects 1e-11. */
+ *                tol + fp32_switch * |E|, when the energy fell by less than
+ *                fp32_switch * |E| per iteration on average over the last 256
+ *                iterations, or when no decrease is found; 0 selects 1e-10. */
 typedef struct {
   int precision;
   int stop;
@@ -205,6 +206,42 @@ gpsoc_status gpsoc_prolong(gpsoc_problem* p, int level);
  * device memory `data` (complex128).  inverse != 0 applies the inverse
  * transform including 1/n (Section 3.2 convention, forward unnormalised). */
 gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, int inverse);
+
+/* Served form: continuous batching of ground-state requests (the paper's method
+ * applied to a stream of independent problems; no counterpart in the paper).
+ * Requests are grouped by grid, trap and stopping rule into buckets of
+ * slots_per_bucket solves that advance together (one CUDA graph replay per two
+ * PCG iterations, each bucket on its own stream).  Every gpsoc_server_step
+ * advances each non-empty bucket by iters_per_step iterations, retires the
+ * solves that stopped and refills free slots from the queue in arrival order;
+ * buckets are created while hbm_budget_bytes allows and released when empty and
+ * the room is needed.  With GPSOC_MIXED a request runs first in FP32 arrays (FP64
+ * sums) and then in FP64 from that iterate to its stopping rule.  Requests are
+ * single-level solves (opts->cm_levels must be 0 or 1) with analytic traps. */
+typedef struct gpsoc_server gpsoc_server;
+typedef struct {
+  double hbm_budget_bytes;   /* device memory the buckets may use */
+  int slots_per_bucket;      /* solves per bucket (0 = 32) */
+  int precision;             /* GPSOC_FP64 or GPSOC_MIXED */
+  int iters_per_step;        /* PCG iterations per bucket and step (0 = 32) */
+} gpsoc_server_opts;
+
+gpsoc_status gpsoc_server_create(const gpsoc_server_opts* opts, gpsoc_server** out);
+void gpsoc_server_destroy(gpsoc_server* s);
+/* Queue one request: psi0 is the host initial guess on the grid (3 * npts complex,
+ * normalised on admission); the arguments are copied.  *ticket identifies it. */
+gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const gpsoc_trap* trap,
+                                 const gpsoc_params* params, const double* psi0, const gpsoc_opts* opts,
+                                 uint64_t* ticket);
+/* Admit, advance, retire (see above).  *busy (may be NULL) receives the number of
+ * requests queued or running. */
+gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy);
+/* GPSOC_OK with the result (and the final wave function in psi_out, may be NULL)
+ * once the request finished -- the ticket is then released; GPSOC_ESTATE while it
+ * is queued or running; GPSOC_EINVAL for an unknown ticket. */
+gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, gpsoc_result* res, double* psi_out);
+/* Device bytes reserved by buckets, number of buckets, queued requests. */
+gpsoc_status gpsoc_server_stats(const gpsoc_server* s, double* bytes_in_use, int* buckets, int* queued);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
  *   gpsoc_profile: run `iters` PCG iterations from the current state (beta

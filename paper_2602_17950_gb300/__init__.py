@@ -6,7 +6,7 @@ The numerical work happens in the CUDA library libgpsoc.so (C ABI in
 include/gpsoc.h); this package only marshals arguments (see `gpsoc`).
 """
 from .gpsoc import (GPSOC_FP64, GPSOC_MIXED, GPSOC_STOP_DPHI, GPSOC_STOP_ENERGY, GPSOC_STOP_RES,
-                    GpsocError, Problem, library, status_name)
+                    GpsocError, Problem, Server, library, status_name)
 
-__all__ = ["Problem", "GpsocError", "library", "status_name", "GPSOC_FP64", "GPSOC_MIXED",
+__all__ = ["Problem", "Server", "GpsocError", "library", "status_name", "GPSOC_FP64", "GPSOC_MIXED",
            "GPSOC_STOP_DPHI", "GPSOC_STOP_RES", "GPSOC_STOP_ENERGY"]

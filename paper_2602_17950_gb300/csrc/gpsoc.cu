@@ -857,7 +857,7 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
       if (s != GPSOC_OK) return s;
     }
     s = run_level(p, lev, o, check, lev == levels - 1, opts->precision,
-                  opts->fp32_switch > 0 ? opts->fp32_switch : 1e-11);
+                  opts->fp32_switch > 0 ? opts->fp32_switch : 1e-10);
     if (s != GPSOC_OK) return s;
     for (int i = 0; i < p->batch; ++i) {
       p->level_iters[i].push_back(p->h_st[i].total_iters - done[i]);
@@ -1108,6 +1108,323 @@ gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, i
   else CL<double>(p, inverse ? COL_INV : COL_FWD, axis, a);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+}  // extern "C"
+
+// =====================================================================================
+// Served form: continuous batching of ground-state requests.
+//
+// Requests are grouped into buckets by (grid, trap, stopping rule, precision
+// stage); a bucket is a problem whose batch entries are slots.  Every step
+// advances each non-empty bucket by a fixed number of PCG iterations (one graph
+// replay per two iterations, each bucket on its own stream so buckets overlap on
+// the device), then retires the slots whose solve stopped and refills free
+// slots from the queue.  New buckets are created while the device-memory budget
+// allows; empty buckets are released when queued requests need the room.
+// With GPSOC_MIXED a request first runs in an FP32-stage bucket (FP32 arrays,
+// FP64 sums) and then, from its FP32 iterate, in an FP64 bucket to the stopping rule.
+// =====================================================================================
+namespace {
+
+struct ServerReq {
+  uint64_t ticket = 0;
+  gpsoc_grid grid{};
+  gpsoc_trap trap{};
+  gpsoc_params par{};
+  gpsoc_opts opts{};
+  std::vector<double> psi;     // initial guess, later the state handed from the FP32 stage, finally the result
+  int stage = 0;               // 1 = FP32 stage, 2 = FP64 stage, 3 = finished
+  int fp32_iters = 0;
+  gpsoc_result res{};
+};
+
+struct Bucket {
+  gpsoc_problem* p = nullptr;
+  std::string key;
+  int stage = 2;
+  OptsDev o{};
+  std::vector<int64_t> slot;   // ticket per slot, -1 = free
+  size_t bytes = 0;
+  int parity = 0;
+};
+
+std::string bucket_key(const ServerReq& r, int stage) {
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%d|%d,%d,%d|%.17g,%.17g,%.17g|%d|%.17g,%.17g,%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d",
+                r.grid.dim, r.grid.n[0], r.grid.n[1], r.grid.n[2], r.grid.L[0], r.grid.L[1], r.grid.L[2], r.trap.kind,
+                r.trap.g[0], r.trap.g[1], r.trap.g[2], r.trap.quad, r.trap.quart, r.opts.stop, r.opts.tol,
+                r.opts.res_tol, r.opts.max_iter, stage);
+  return buf;
+}
+
+size_t solve_points(const gpsoc_grid& g) {
+  size_t n = 1;
+  for (int i = 0; i < g.dim; ++i) n *= (size_t)g.n[i];
+  return n;
+}
+
+}  // namespace
+
+struct gpsoc_server {
+  gpsoc_server_opts opts{};
+  std::vector<Bucket*> buckets;
+  std::map<uint64_t, ServerReq*> reqs;
+  std::vector<uint64_t> queue;   // FIFO of tickets waiting for a slot
+  size_t bytes = 0;
+  uint64_t next = 1;
+};
+
+namespace {
+
+size_t bucket_bytes(const gpsoc_grid& g, int slots, int stage) {
+  const size_t per = sizeof(double2) * 3 * solve_points(g);
+  size_t b = 12 * per * (size_t)slots;                     // FP64 working set
+  if (stage == 1) b += 12 * (per / 2) * (size_t)slots;     // FP32 working set
+  return b + (4u << 20);
+}
+
+gpsoc_status load_slot(Bucket* b, int s, const ServerReq& r) {
+  gpsoc_problem* p = b->p;
+  const Geo g = make_geo(p, 0);
+  const size_t off = (size_t)s * 3 * g.npts;
+  CK(cudaMemcpyAsync(p->b64.Phi + off, r.psi.data(), sizeof(double2) * 3 * g.npts, cudaMemcpyHostToDevice, p->stream));
+  const PhysDev ph{r.par.Omega, r.par.gamma, r.par.beta0, r.par.beta1};
+  CK(cudaMemcpyAsync(p->d_phys + s, &ph, sizeof(PhysDev), cudaMemcpyHostToDevice, p->stream));
+  ElemArgs<double> e = elem_args<double>(p, g, GATE_ALL);
+  e.only = s;
+  e.in0 = p->b64.Phi;
+  EL<double>(p, EL_MASS, e);
+  ScalarArgs x = scalar_args(p, 0, PH_NORM, g);
+  x.only = s;
+  SL(p, x);
+  e.out0 = p->b64.Phi;
+  EL<double>(p, EL_SCALE, e);
+  ScalarArgs in = scalar_args(p, 0, PH_INIT, g);
+  in.only = s;
+  in.flags = 1;
+  SL(p, in);
+  if (b->stage == 1) {
+    launch_convert<float>(p->b64.Phi + off, 0, p->b32.Phi + off, (long long)3 * g.npts, p->stream);
+    mark(p, "convert");
+  }
+  CK(cudaGetLastError());
+  // the PCG state of this slot is per solve (first = 1 restarts beta); host parameters follow
+  p->params[s] = r.par;
+  return GPSOC_OK;
+}
+
+gpsoc_status read_slot(Bucket* b, int s, ServerReq& r) {
+  gpsoc_problem* p = b->p;
+  const Geo g = make_geo(p, 0);
+  const size_t off = (size_t)s * 3 * g.npts;
+  if (b->stage == 1) {
+    launch_convert<double>(p->b32.Phi + off, 1, p->b64.Phi + off, (long long)3 * g.npts, p->stream);
+    mark(p, "convert");
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(r.psi.data(), p->b64.Phi + off, sizeof(double2) * 3 * g.npts, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_status* err) {
+  const std::string key = bucket_key(r, stage);
+  for (Bucket* b : sv->buckets) {
+    if (b->key != key) continue;
+    for (int64_t t : b->slot)
+      if (t < 0) return b;
+  }
+  const int slots = sv->opts.slots_per_bucket > 0 ? sv->opts.slots_per_bucket : 32;
+  const size_t need = bucket_bytes(r.grid, slots, stage);
+  // release empty buckets while the budget is short
+  for (size_t i = 0; i < sv->buckets.size() && sv->bytes + need > (size_t)sv->opts.hbm_budget_bytes;) {
+    Bucket* b = sv->buckets[i];
+    bool empty = true;
+    for (int64_t t : b->slot) empty &= (t < 0);
+    if (empty) {
+      gpsoc_destroy(b->p);
+      sv->bytes -= b->bytes;
+      delete b;
+      sv->buckets.erase(sv->buckets.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+  if (sv->bytes + need > (size_t)sv->opts.hbm_budget_bytes) return nullptr;   // wait for room
+  Bucket* b = new Bucket();
+  std::vector<gpsoc_params> pars(slots, r.par);
+  gpsoc_status s = gpsoc_create(&r.grid, &r.trap, pars.data(), slots, nullptr, &b->p);
+  if (s != GPSOC_OK) { delete b; *err = s; return nullptr; }
+  if (stage == 1 && ensure_fp32(b->p) != GPSOC_OK) { gpsoc_destroy(b->p); delete b; *err = GPSOC_ENOMEM; return nullptr; }
+  b->key = key;
+  b->stage = stage;
+  b->slot.assign(slots, -1);
+  b->bytes = need;
+  b->o = make_opts(&r.opts);
+  if (stage == 1) {
+    b->o.stop = GPSOC_STOP_ENERGY;
+    b->o.res_tol = 0.0;
+    b->o.tol_rel = r.opts.fp32_switch > 0 ? r.opts.fp32_switch : 1e-10;
+    b->o.phase32 = 1;
+  }
+  // every slot starts inactive (gpsoc_create zeroes the per-solve states)
+  b->p->level = 0;
+  b->p->has_state = true;
+  sv->bytes += need;
+  sv->buckets.push_back(b);
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpsoc_status gpsoc_server_create(const gpsoc_server_opts* opts, gpsoc_server** out) {
+  g_err.clear();
+  if (!opts || !out) return fail(GPSOC_EINVAL, "NULL argument");
+  if (!(opts->hbm_budget_bytes > 0)) return fail(GPSOC_EINVAL, "hbm_budget_bytes must be > 0");
+  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
+  gpsoc_server* s = new gpsoc_server();
+  s->opts = *opts;
+  *out = s;
+  return GPSOC_OK;
+}
+
+void gpsoc_server_destroy(gpsoc_server* s) {
+  if (!s) return;
+  for (Bucket* b : s->buckets) { gpsoc_destroy(b->p); delete b; }
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+}
+
+gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const gpsoc_trap* trap,
+                                 const gpsoc_params* params, const double* psi0, const gpsoc_opts* opts,
+                                 uint64_t* ticket) {
+  g_err.clear();
+  if (!s || !grid || !trap || !params || !psi0 || !opts || !ticket) return fail(GPSOC_EINVAL, "NULL argument");
+  if (trap->kind == GPSOC_TRAP_USER) return fail(GPSOC_EINVAL, "the server takes analytic traps only");
+  if (opts->cm_levels > 1) return fail(GPSOC_EINVAL, "the server runs single-level solves (cm_levels = 1)");
+  if (!(opts->tol > 0)) return fail(GPSOC_EINVAL, "tol must be > 0");
+  for (int i = 0; i < grid->dim; ++i)
+    if (!pow2(grid->n[i]) || grid->n[i] < 8 || grid->n[i] > 1024) return fail(GPSOC_EINVAL, "grid sizes must be powers of two in [8, 1024]");
+  if (grid->dim != 2 && grid->dim != 3) return fail(GPSOC_EINVAL, "dim must be 2 or 3");
+  ServerReq* r = new ServerReq();
+  r->ticket = s->next++;
+  r->grid = *grid;
+  for (int i = grid->dim; i < 3; ++i) { r->grid.n[i] = 1; r->grid.L[i] = 1.0; }
+  r->trap = *trap;
+  r->trap.user_V = nullptr;
+  r->par = *params;
+  r->opts = *opts;
+  r->psi.assign(psi0, psi0 + 2 * 3 * solve_points(r->grid));
+  r->stage = (s->opts.precision == GPSOC_MIXED) ? 1 : 2;
+  s->reqs[r->ticket] = r;
+  s->queue.push_back(r->ticket);
+  *ticket = r->ticket;
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
+  g_err.clear();
+  if (!s) return fail(GPSOC_EINVAL, "NULL server");
+  gpsoc_status err = GPSOC_OK;
+  // admission: fill free slots from the queue, in arrival order
+  std::vector<uint64_t> waiting;
+  for (uint64_t t : s->queue) {
+    ServerReq* r = s->reqs[t];
+    Bucket* b = find_or_make_bucket(s, *r, r->stage, &err);
+    if (err != GPSOC_OK) return err;
+    if (!b) { waiting.push_back(t); continue; }
+    int slot = -1;
+    for (size_t k = 0; k < b->slot.size(); ++k)
+      if (b->slot[k] < 0) { slot = (int)k; break; }
+    gpsoc_status st = load_slot(b, slot, *r);
+    if (st != GPSOC_OK) return st;
+    b->slot[slot] = (int64_t)t;
+  }
+  s->queue.swap(waiting);
+  // advance every bucket that holds work; buckets run on their own streams
+  const int iters = s->opts.iters_per_step > 0 ? s->opts.iters_per_step : 32;
+  const int pairs = (iters + 1) / 2;
+  for (Bucket* b : s->buckets) {
+    bool any = false;
+    for (int64_t t : b->slot) any |= (t >= 0);
+    if (!any) continue;
+    const int k = (b->stage == 1) ? 1 : 0;
+    gpsoc_status st = (k == 1) ? build_graph<float>(b->p, 0, b->o) : build_graph<double>(b->p, 0, b->o);
+    if (st != GPSOC_OK) return st;
+    for (int r = 0; r < pairs; ++r) {
+      CK(cudaGraphLaunch(b->p->graph[k], b->p->stream));
+      b->p->launches += b->p->graph_kernels[k];
+    }
+  }
+  // retire stopped solves
+  int n_busy = 0;
+  for (Bucket* b : s->buckets) {
+    bool any = false;
+    for (int64_t t : b->slot) any |= (t >= 0);
+    if (!any) continue;
+    gpsoc_status st = sync_state(b->p);
+    if (st != GPSOC_OK) return st;
+    for (size_t k = 0; k < b->slot.size(); ++k) {
+      if (b->slot[k] < 0) continue;
+      const SolveState& S = b->p->h_st[k];
+      if (S.active) { ++n_busy; continue; }
+      ServerReq* r = s->reqs[(uint64_t)b->slot[k]];
+      st = read_slot(b, (int)k, *r);
+      if (st != GPSOC_OK) return st;
+      b->slot[k] = -1;
+      if (b->stage == 1) {                 // FP32 stage done: continue in FP64 from this iterate
+        r->fp32_iters = S.iters;
+        r->stage = 2;
+        s->queue.push_back(r->ticket);
+        ++n_busy;
+        continue;
+      }
+      gpsoc_result& o = r->res;
+      o.status = S.status;
+      o.iters = S.iters;
+      o.total_iters = S.iters + r->fp32_iters;
+      o.levels = 1;
+      o.beta_resets = S.beta_resets;
+      o.halvings = S.halvings;
+      o.fp32_iters = r->fp32_iters;
+      o.fp64_iters = S.iters;
+      o.energy = S.E;
+      o.mu = S.mu;
+      for (int c = 0; c < 3; ++c) o.mass[c] = S.mass[c];
+      o.res_inf = S.res_inf;
+      o.dE_last = S.dE_last;
+      o.level_iters[0] = o.total_iters;
+      r->stage = 3;
+    }
+  }
+  n_busy += (int)s->queue.size();
+  if (busy) *busy = n_busy;
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, gpsoc_result* res, double* psi_out) {
+  g_err.clear();
+  if (!s) return fail(GPSOC_EINVAL, "NULL server");
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return fail(GPSOC_EINVAL, "unknown ticket");
+  ServerReq* r = it->second;
+  if (r->stage != 3) return GPSOC_ESTATE;   // still queued or running (no message: polling is routine)
+  if (res) *res = r->res;
+  if (psi_out) std::memcpy(psi_out, r->psi.data(), sizeof(double) * r->psi.size());
+  delete r;
+  s->reqs.erase(it);
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_server_stats(const gpsoc_server* s, double* bytes_in_use, int* buckets, int* queued) {
+  if (!s) return GPSOC_EINVAL;
+  if (bytes_in_use) *bytes_in_use = (double)s->bytes;
+  if (buckets) *buckets = (int)s->buckets.size();
+  if (queued) *queued = (int)s->queue.size();
   return GPSOC_OK;
 }
 

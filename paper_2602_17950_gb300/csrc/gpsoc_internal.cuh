@@ -65,7 +65,7 @@ struct SolveState {
   int beta_resets, halvings;
   int fp32_iters, fp64_iters;
   int pending;      // an accepted step waits to be applied by the next iteration's first pass
-  int pad1;
+  int it_win;       // FP32 phase: iteration at which the current stall window opened
   // observables of the current iterate
   double E, mu, Q;          // energy, chemical potential, <H_lin Phi, Phi>
   double rho2, F2;          // sum rho^2, sum |F|^2 (times dV)
@@ -77,6 +77,7 @@ struct SolveState {
   double I[6], J[6];
   double a, b, theta, dE, dE_last;
   double upd_c, upd_s, upd_scale;
+  double E_win;     // FP32 phase: energy when the stall window opened
 };
 
 struct OptsDev {

@@ -32,6 +32,7 @@ struct ScalarArgs {
   double* norm_scale;
   int force;          // process every solve regardless of its active flag
   const double* thetas; int n_theta; double* model_out;
+  int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
 };
 
 enum ElemMode { EL_DIR = 0, EL_UPDATE, EL_MASS, EL_SCALE };
@@ -51,6 +52,7 @@ struct ElemArgs {
   int fuse;           // EL_DIR: the last block runs the PH_CPROJ step
   unsigned* cnt;
   ScalarCtx sc;
+  int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
 };
 
 void launch_scalar(const ScalarArgs& a, cudaStream_t st);

@@ -23,13 +23,14 @@ __global__ void k_scalar(ScalarArgs A) {
   if (s >= A.nsolve) return;
   SolveState& S = A.st[s];
   const int ph_ = A.phase;
+  if (A.only >= 0 && s != A.only) return;
   if (ph_ != PH_INIT && ph_ != PH_NORM && !A.force && !S.active) return;
   ScalarCtx X{A.st, A.phys, A.part, A.pmax, A.nb_row, A.nb_col, A.npts, A.dV, A.opts, A.flags};
   switch (ph_) {
     case PH_INIT:
       if (threadIdx.x == 0) {
         S.active = 1; S.status = GPSOC_OK; S.iters = 0; S.first = 1; S.reset = 0; S.pending = 0;
-        S.dE_last = nan(""); S.dphi_inf = nan("");
+        S.dE_last = nan(""); S.dphi_inf = nan(""); S.E_win = INFINITY; S.it_win = 0;
         if (A.flags & 1) { S.total_iters = 0; S.beta_resets = 0; S.halvings = 0; S.fp32_iters = 0; S.fp64_iters = 0; }
       }
       return;
@@ -71,6 +72,7 @@ __global__ void k_elem(ElemArgs<T> A) {
   const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
   if (s >= A.nsolve) return;
   const SolveState& S = A.st[s];
+  if (A.only >= 0 && s != A.only) return;
   if (!gate_ok(A.st, A.gate, s)) return;
   const long long npts = A.npts;
   const long long per = npts / bps;

@@ -71,6 +71,8 @@ __device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratc
     deactivate(S, GPSOC_ENONFINITE);
 }
 
+constexpr int kStallWindow = 256;
+
 // max_l ||r_l||_inf and the stopping test (Eqs. stop1-stop3)
 __device__ __forceinline__ void sc_res(const ScalarCtx& X, int s, double* scratch) {
   SolveState& S = X.st[s];
@@ -87,6 +89,14 @@ __device__ __forceinline__ void sc_res(const ScalarCtx& X, int s, double* scratc
     else conv = S.dphi_inf < O.tol;
     if (conv && O.res_tol > 0.0) conv = rinf < O.res_tol;
     if (conv) { S.active = 0; return; }
+  }
+  // FP32 phase: per-iteration energy changes carry rounding noise that can stay
+  // above tol_rel |E| for ever; hand over to FP64 once the energy fell by less
+  // than tol_rel |E| per iteration on average over a window of kStallWindow.
+  if (O.phase32 && S.iters - S.it_win >= kStallWindow) {
+    if (!(S.E_win - S.E >= kStallWindow * O.tol_rel * fabs(S.E))) { S.active = 0; return; }
+    S.E_win = S.E;
+    S.it_win = S.iters;
   }
   if (S.iters >= O.max_iter) {
     if (O.phase32) S.active = 0;

@@ -63,6 +63,11 @@ class Result(C.Structure):
                 "level_iters": list(self.level_iters[:max(self.levels, 1)])}
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("slots_per_bucket", C.c_int), ("precision", C.c_int),
+                ("iters_per_step", C.c_int)]
+
+
 _lib = None
 
 _PROTOS = {
@@ -89,6 +94,13 @@ _PROTOS = {
     "gpsoc_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gpsoc_apply_h_noalloc": (C.c_int, [C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_int, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gpsoc_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "gpsoc_server_destroy": (None, [C.c_void_p]),
+    "gpsoc_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_void_p,
+                                      C.POINTER(Opts), C.POINTER(C.c_uint64)]),
+    "gpsoc_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "gpsoc_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_void_p]),
+    "gpsoc_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "gpsoc_last_error": (C.c_char_p, []),
     "gpsoc_version": (C.c_char_p, []),
 }
@@ -303,3 +315,77 @@ class Problem:
 
     def fft_axis(self, data_dptr: int, count: int, axis: int, inverse=False):
         _check(library().gpsoc_fft_axis(self._h, C.c_void_p(data_dptr), count, axis, int(inverse)))
+
+
+def _grid_trap(n, L, trap):
+    dim = len(n)
+    g = Grid(dim, (C.c_int * 3)(*(list(n) + [1] * (3 - dim))), (C.c_double * 3)(*(list(L) + [1.0] * (3 - dim))))
+    trap = dict(trap or {})
+    gv = list(trap.get("g", (1.0, 1.0, 1.0))) + [1.0] * 3
+    t = Trap(int(trap.get("kind", 0)), (C.c_double * 3)(*gv[:3]), float(trap.get("quad", 0.0)),
+             float(trap.get("quart", 0.0)), None)
+    return g, t
+
+
+class Server:
+    """Continuous-batching request server (gpsoc_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=120e9, slots_per_bucket=32, precision=GPSOC_FP64, iters_per_step=32):
+        o = ServerOpts(float(hbm_budget_bytes), int(slots_per_bucket), int(precision), int(iters_per_step))
+        h = C.c_void_p()
+        _check(library().gpsoc_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().gpsoc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, n, L, params, psi0, trap=None, **opts):
+        g, t = _grid_trap(n, L, trap)
+        par = Params(*map(float, params))
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128).reshape((3,) + tuple(n[::-1]))
+        o = Problem.opts(**opts)
+        tk = C.c_uint64(0)
+        _check(library().gpsoc_server_submit(self._h, C.byref(g), C.byref(t), C.byref(par), _ptr(psi0), C.byref(o),
+                                             C.byref(tk)))
+        self._shapes[tk.value] = (3,) + tuple(n[::-1])
+        return tk.value
+
+    def step(self) -> int:
+        busy = C.c_int(0)
+        _check(library().gpsoc_server_step(self._h, C.byref(busy)))
+        return busy.value
+
+    def poll(self, ticket, want_psi=True):
+        """(result dict, psi) once finished, else None."""
+        res = Result()
+        shape = self._shapes.get(ticket)    # unknown tickets are rejected by the library
+        psi = np.empty(shape, dtype=np.complex128) if want_psi and shape is not None else None
+        code = library().gpsoc_server_poll(self._h, C.c_uint64(ticket), C.byref(res),
+                                           _ptr(psi) if psi is not None else None)
+        if code == 7:
+            return None
+        _check(code)
+        self._shapes.pop(ticket, None)
+        return res.as_dict(), psi
+
+    def stats(self):
+        b = C.c_double(0)
+        nb = C.c_int(0)
+        q = C.c_int(0)
+        _check(library().gpsoc_server_stats(self._h, C.byref(b), C.byref(nb), C.byref(q)))
+        return {"bytes_in_use": b.value, "buckets": nb.value, "queued": q.value}
