@@ -365,6 +365,93 @@ def batch_case(args):
     print(json.dumps(out))
 
 
+def serve_case(args):
+    """The served trace: `requests` ground-state requests with Poisson arrivals,
+    grids drawn from {64^2, 128^2, 256^2, 512^2, 64^3, 128^3}, parameters drawn as
+    in the batched sweep, harmonic traps (3D: gamma_z = 2), stop |dE| < serve_tol.
+    Three arms on the same trace: the continuous-batching server in mixed
+    precision and in FP64, and plain single-solve FP64 PCG serving the requests
+    one at a time in arrival order.  Reports solves/s over the makespan and the
+    p50/p99 of arrival-to-result latency (wall clock)."""
+    import torch
+    from paper_2602_17950_gb300 import Problem, Server
+    from paper_2602_17950_gb300.build import build
+    build()
+    trace = si.serve_trace(si.seed_for(5, 0), args.requests, args.arrival_rate)
+    R = len(trace)
+    guesses = [si.gaussian_guess(q["n"], q["L"], q["guess_seed"], vortex=q["vortex"]) for q in trace]
+    traps = [{"kind": 0, "g": (1.0, 1.0, 2.0) if len(q["n"]) == 3 else (1.0, 1.0)} for q in trace]
+    opts = dict(tol=args.serve_tol, max_iter=args.max_iter)
+
+    def par(q):
+        p = q["params"]
+        return (p.Omega, p.gamma, p.beta0, p.beta1)
+
+    def summarise(lat, span, res):
+        ok = sum(r["status"] == "OK" for r in res)
+        return {"solves_per_s": R / span, "makespan_s": span, "converged": ok,
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "iters_mean": float(np.mean([r["total_iters"] for r in res]))}
+
+    def served(precision):
+        done, res = {}, [None] * R
+        with Server(hbm_budget_bytes=args.hbm_budget, slots_per_bucket=args.slots, precision=precision,
+                    iters_per_step=32) as sv:
+            t0 = time.perf_counter()
+            nxt, tickets = 0, {}
+            while len(done) < R:
+                now = time.perf_counter() - t0
+                while nxt < R and trace[nxt]["arrival"] <= now:
+                    q = trace[nxt]
+                    tickets[sv.submit(q["n"], q["L"], par(q), guesses[nxt], trap=traps[nxt], **opts)] = nxt
+                    nxt += 1
+                busy = sv.step()
+                for t, k in list(tickets.items()):
+                    got = sv.poll(t, want_psi=False)
+                    if got is not None:
+                        done[k] = time.perf_counter() - t0
+                        res[k] = got[0]
+                        del tickets[t]
+                if busy == 0 and nxt < R:
+                    time.sleep(max(0.0, trace[nxt]["arrival"] - (time.perf_counter() - t0)))
+            span = max(done.values())
+        lat = [done[k] - trace[k]["arrival"] for k in range(R)]
+        return summarise(lat, span, res), res
+
+    def plain():
+        res, lat = [None] * R, [0.0] * R
+        t0 = time.perf_counter()
+        for k, q in enumerate(trace):
+            wait = q["arrival"] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            with Problem(q["n"], q["L"], [par(q)], trap=traps[k]) as p:
+                p.set_initial(guesses[k][None])
+                res[k] = p.solve(raise_on_error=False, precision=0, **opts)[0]
+            torch.cuda.synchronize()
+            lat[k] = time.perf_counter() - t0 - q["arrival"]
+        span = time.perf_counter() - t0
+        return summarise(lat, span, res), res
+
+    out = {"serve_case": f"{R} requests, Poisson {args.arrival_rate}/s, grids 64^2..512^2, 64^3, 128^3, "
+                         f"stop |dE|<{args.serve_tol:g}, max_iter {args.max_iter}",
+           "grid_mix": {f"{'x'.join(map(str, n))}": sum(q["n"] == n for q in trace) for n, _ in si.SERVE_GRIDS},
+           "hbm_budget_gb": args.hbm_budget / 1e9, "slots_per_bucket": args.slots}
+    arms = {}
+    for name, fn in (("served_mixed", lambda: served(1)), ("served_fp64", lambda: served(0)), ("plain_fp64", plain)):
+        if name in args.arms.split(","):
+            out[name], arms[name] = fn()
+    if "plain_fp64" in arms:
+        ref = arms["plain_fp64"]
+        for name, rs in arms.items():
+            if name != "plain_fp64":
+                d = [abs(a["energy"] - b["energy"]) / abs(b["energy"]) for a, b in zip(rs, ref)
+                     if a["status"] == "OK" and b["status"] == "OK"]
+                out[name]["energy_rel_diff_vs_plain_max"] = float(max(d)) if d else None
+                out[name]["speedup_vs_plain"] = out[name]["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
+    print(json.dumps(out))
+
+
 def kernel_case(args):
     """Per-kernel durations of PCG iterations of `batch` solves on an N x N grid of
     the bench workload (box, trap, parameters), CUDA events on the solver's stream.
@@ -409,8 +496,18 @@ def main():
                     help="only time the kernels of PCG iterations on N x N grids (per-kernel CUDA events)")
     ap.add_argument("--batch", type=int, default=1, help="solves per problem in --kernel-case / --batch-case")
     ap.add_argument("--batch-case", action="store_true", help="the batched random-parameter sweep at 256^2")
-    ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of --batch-case")
+    ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of --batch-case / --serve-case")
+    ap.add_argument("--serve-case", action="store_true", help="the served trace (Poisson arrivals, mixed grids)")
+    ap.add_argument("--requests", type=int, default=32, help="requests of --serve-case")
+    ap.add_argument("--arrival-rate", type=float, default=4.0, help="Poisson arrival rate of --serve-case (1/s)")
+    ap.add_argument("--serve-tol", type=float, default=1e-10, help="energy stopping tolerance of --serve-case")
+    ap.add_argument("--hbm-budget", type=float, default=120e9, help="device bytes the server may use")
+    ap.add_argument("--slots", type=int, default=16, help="solves per server bucket")
+    ap.add_argument("--arms", default="served_mixed,served_fp64,plain_fp64", help="arms of --serve-case")
     args = ap.parse_args()
+    if args.serve_case:
+        serve_case(args)
+        return
     if args.batch_case:
         batch_case(args)
         return

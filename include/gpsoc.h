@@ -96,7 +96,11 @@ typedef struct {
  *                accepted step changes the energy by less than
  *                tol + fp32_switch * |E|, when the energy fell by less than
  *                fp32_switch * |E| per iteration on average over the last 256
- *                iterations, or when no decrease is found; 0 selects 1e-10. */
+ *                iterations, or when no decrease is found; 0 selects 1e-10.
+ *   fp32_min_points  GPSOC_MIXED only: a level (or server bucket) whose solves x
+ *                grid points fall below this runs in FP64 alone, since FP32
+ *                arrays save little on work that is bound by launch latency;
+ *                0 selects 65536, a negative value gives every level an FP32 phase. */
 typedef struct {
   int precision;
   int stop;
@@ -108,6 +112,7 @@ typedef struct {
   int cm_levels;
   int check_every;
   double fp32_switch;
+  int fp32_min_points;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;
@@ -210,12 +215,14 @@ gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, i
 /* Served form: continuous batching of ground-state requests (the paper's method
  * applied to a stream of independent problems; no counterpart in the paper).
  * Requests are grouped by grid, trap and stopping rule into buckets of
- * slots_per_bucket solves that advance together (one CUDA graph replay per two
- * PCG iterations, each bucket on its own stream).  Every gpsoc_server_step
- * advances each non-empty bucket by iters_per_step iterations, retires the
- * solves that stopped and refills free slots from the queue in arrival order;
- * buckets are created while hbm_budget_bytes allows and released when empty and
- * the room is needed.  With GPSOC_MIXED a request runs first in FP32 arrays (FP64
+ * slots_per_bucket solves that advance together in rounds of iters_per_step PCG
+ * iterations (one CUDA graph replay per two iterations), each bucket on its own
+ * stream and at its own pace.  gpsoc_server_step retires the solves that stopped
+ * in every bucket whose round has finished (waiting for the earliest-launched
+ * round if none has), refills free slots from the queue in arrival order, and
+ * starts the next round of every idle bucket that holds work; it returns while
+ * rounds run.  Buckets are created while hbm_budget_bytes allows and released
+ * when empty, idle and the room is needed.  With GPSOC_MIXED a request runs first in FP32 arrays (FP64
  * sums) and then in FP64 from that iterate to its stopping rule.  Requests are
  * single-level solves (opts->cm_levels must be 0 or 1) with analytic traps. */
 typedef struct gpsoc_server gpsoc_server;
@@ -233,8 +240,8 @@ void gpsoc_server_destroy(gpsoc_server* s);
 gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const gpsoc_trap* trap,
                                  const gpsoc_params* params, const double* psi0, const gpsoc_opts* opts,
                                  uint64_t* ticket);
-/* Admit, advance, retire (see above).  *busy (may be NULL) receives the number of
- * requests queued or running. */
+/* Retire, admit, launch (see above).  *busy (may be NULL) receives the number of
+ * requests queued or running.  Not thread-safe: one caller per server. */
 gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy);
 /* GPSOC_OK with the result (and the final wave function in psi_out, may be NULL)
  * once the request finished -- the ticket is then released; GPSOC_ESTATE while it

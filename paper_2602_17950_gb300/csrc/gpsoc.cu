@@ -563,6 +563,18 @@ gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_
   return iterate_until_done<double>(p, level, o, check_every);
 }
 
+// MIXED runs an FP32 phase only where the work per iteration is large enough
+// for FP32 arrays to pay (fp32_min_points, default 65536 solve-points).
+long long mixed_min_points(const gpsoc_opts* opts) {
+  return opts->fp32_min_points > 0 ? opts->fp32_min_points : opts->fp32_min_points < 0 ? 0 : 65536;
+}
+
+int level_precision(const gpsoc_problem* p, int level, const gpsoc_opts* opts) {
+  if (opts->precision != GPSOC_MIXED) return GPSOC_FP64;
+  const Geo g = make_geo(p, level);
+  return (long long)p->batch * g.npts >= mixed_min_points(opts) ? GPSOC_MIXED : GPSOC_FP64;
+}
+
 gpsoc_status normalize(gpsoc_problem* p, int level) {
   const Geo g = make_geo(p, level);
   ElemArgs<double> e = elem_args<double>(p, g, GATE_ALL);
@@ -856,7 +868,7 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
       s = prolong_impl(p, lev + 1);
       if (s != GPSOC_OK) return s;
     }
-    s = run_level(p, lev, o, check, lev == levels - 1, opts->precision,
+    s = run_level(p, lev, o, check, lev == levels - 1, level_precision(p, lev, opts),
                   opts->fp32_switch > 0 ? opts->fp32_switch : 1e-10);
     if (s != GPSOC_OK) return s;
     for (int i = 0; i < p->batch; ++i) {
@@ -1147,8 +1159,22 @@ struct Bucket {
   OptsDev o{};
   std::vector<int64_t> slot;   // ticket per slot, -1 = free
   size_t bytes = 0;
-  int parity = 0;
+  cudaEvent_t done = nullptr;  // recorded after the last launched round of iterations
+  bool in_flight = false;
+  uint64_t launched = 0;       // launch sequence number of the round in flight
 };
+
+bool bucket_empty(const Bucket* b) {
+  for (int64_t t : b->slot)
+    if (t >= 0) return false;
+  return true;
+}
+
+void bucket_free(Bucket* b) {
+  if (b->done) cudaEventDestroy(b->done);
+  gpsoc_destroy(b->p);
+  delete b;
+}
 
 std::string bucket_key(const ServerReq& r, int stage) {
   char buf[512];
@@ -1174,6 +1200,7 @@ struct gpsoc_server {
   std::vector<uint64_t> queue;   // FIFO of tickets waiting for a slot
   size_t bytes = 0;
   uint64_t next = 1;
+  uint64_t rounds = 0;           // rounds of iterations launched, over all buckets
 };
 
 namespace {
@@ -1238,15 +1265,12 @@ Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_sta
   }
   const int slots = sv->opts.slots_per_bucket > 0 ? sv->opts.slots_per_bucket : 32;
   const size_t need = bucket_bytes(r.grid, slots, stage);
-  // release empty buckets while the budget is short
+  // release idle empty buckets while the budget is short
   for (size_t i = 0; i < sv->buckets.size() && sv->bytes + need > (size_t)sv->opts.hbm_budget_bytes;) {
     Bucket* b = sv->buckets[i];
-    bool empty = true;
-    for (int64_t t : b->slot) empty &= (t < 0);
-    if (empty) {
-      gpsoc_destroy(b->p);
+    if (bucket_empty(b) && !b->in_flight) {
       sv->bytes -= b->bytes;
-      delete b;
+      bucket_free(b);
       sv->buckets.erase(sv->buckets.begin() + i);
     } else {
       ++i;
@@ -1257,7 +1281,13 @@ Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_sta
   std::vector<gpsoc_params> pars(slots, r.par);
   gpsoc_status s = gpsoc_create(&r.grid, &r.trap, pars.data(), slots, nullptr, &b->p);
   if (s != GPSOC_OK) { delete b; *err = s; return nullptr; }
-  if (stage == 1 && ensure_fp32(b->p) != GPSOC_OK) { gpsoc_destroy(b->p); delete b; *err = GPSOC_ENOMEM; return nullptr; }
+  if (stage == 1 && ensure_fp32(b->p) != GPSOC_OK) { bucket_free(b); *err = GPSOC_ENOMEM; return nullptr; }
+  if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    b->done = nullptr;
+    bucket_free(b);
+    *err = fail(GPSOC_ECUDA, "event create failed");
+    return nullptr;
+  }
   b->key = key;
   b->stage = stage;
   b->slot.assign(slots, -1);
@@ -1294,7 +1324,7 @@ gpsoc_status gpsoc_server_create(const gpsoc_server_opts* opts, gpsoc_server** o
 
 void gpsoc_server_destroy(gpsoc_server* s) {
   if (!s) return;
-  for (Bucket* b : s->buckets) { gpsoc_destroy(b->p); delete b; }
+  for (Bucket* b : s->buckets) bucket_free(b);
   for (auto& kv : s->reqs) delete kv.second;
   delete s;
 }
@@ -1319,7 +1349,9 @@ gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const 
   r->par = *params;
   r->opts = *opts;
   r->psi.assign(psi0, psi0 + 2 * 3 * solve_points(r->grid));
-  r->stage = (s->opts.precision == GPSOC_MIXED) ? 1 : 2;
+  const int slots = s->opts.slots_per_bucket > 0 ? s->opts.slots_per_bucket : 32;
+  const bool fp32_pays = (long long)slots * (long long)solve_points(r->grid) >= mixed_min_points(opts);
+  r->stage = (s->opts.precision == GPSOC_MIXED && fp32_pays) ? 1 : 2;
   s->reqs[r->ticket] = r;
   s->queue.push_back(r->ticket);
   *ticket = r->ticket;
@@ -1330,48 +1362,27 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
   g_err.clear();
   if (!s) return fail(GPSOC_EINVAL, "NULL server");
   gpsoc_status err = GPSOC_OK;
-  // admission: fill free slots from the queue, in arrival order
-  std::vector<uint64_t> waiting;
-  for (uint64_t t : s->queue) {
-    ServerReq* r = s->reqs[t];
-    Bucket* b = find_or_make_bucket(s, *r, r->stage, &err);
-    if (err != GPSOC_OK) return err;
-    if (!b) { waiting.push_back(t); continue; }
-    int slot = -1;
-    for (size_t k = 0; k < b->slot.size(); ++k)
-      if (b->slot[k] < 0) { slot = (int)k; break; }
-    gpsoc_status st = load_slot(b, slot, *r);
-    if (st != GPSOC_OK) return st;
-    b->slot[slot] = (int64_t)t;
-  }
-  s->queue.swap(waiting);
-  // advance every bucket that holds work; buckets run on their own streams
-  const int iters = s->opts.iters_per_step > 0 ? s->opts.iters_per_step : 32;
-  const int pairs = (iters + 1) / 2;
+  // 1. buckets whose round of iterations finished: retire the solves that stopped.
+  //    If no bucket has finished yet, wait for the one launched first.
+  bool any_done = false;
+  Bucket* oldest = nullptr;
   for (Bucket* b : s->buckets) {
-    bool any = false;
-    for (int64_t t : b->slot) any |= (t >= 0);
-    if (!any) continue;
-    const int k = (b->stage == 1) ? 1 : 0;
-    gpsoc_status st = (k == 1) ? build_graph<float>(b->p, 0, b->o) : build_graph<double>(b->p, 0, b->o);
-    if (st != GPSOC_OK) return st;
-    for (int r = 0; r < pairs; ++r) {
-      CK(cudaGraphLaunch(b->p->graph[k], b->p->stream));
-      b->p->launches += b->p->graph_kernels[k];
-    }
+    if (!b->in_flight) continue;
+    const cudaError_t q = cudaEventQuery(b->done);
+    if (q == cudaSuccess) { any_done = true; continue; }
+    if (q != cudaErrorNotReady) return fail(GPSOC_ECUDA, std::string("bucket event: ") + cudaGetErrorString(q));
+    if (!oldest || b->launched < oldest->launched) oldest = b;
   }
-  // retire stopped solves
-  int n_busy = 0;
+  if (!any_done && oldest) CK(cudaEventSynchronize(oldest->done));
   for (Bucket* b : s->buckets) {
-    bool any = false;
-    for (int64_t t : b->slot) any |= (t >= 0);
-    if (!any) continue;
+    if (!b->in_flight || cudaEventQuery(b->done) != cudaSuccess) continue;
+    b->in_flight = false;
     gpsoc_status st = sync_state(b->p);
     if (st != GPSOC_OK) return st;
     for (size_t k = 0; k < b->slot.size(); ++k) {
       if (b->slot[k] < 0) continue;
       const SolveState& S = b->p->h_st[k];
-      if (S.active) { ++n_busy; continue; }
+      if (S.active) continue;
       ServerReq* r = s->reqs[(uint64_t)b->slot[k]];
       st = read_slot(b, (int)k, *r);
       if (st != GPSOC_OK) return st;
@@ -1380,7 +1391,6 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
         r->fp32_iters = S.iters;
         r->stage = 2;
         s->queue.push_back(r->ticket);
-        ++n_busy;
         continue;
       }
       gpsoc_result& o = r->res;
@@ -1401,7 +1411,40 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
       r->stage = 3;
     }
   }
-  n_busy += (int)s->queue.size();
+  // 2. admission: fill free slots from the queue, in arrival order (a slot load is
+  //    stream-ordered after any round still running in its bucket)
+  std::vector<uint64_t> waiting;
+  for (uint64_t t : s->queue) {
+    ServerReq* r = s->reqs[t];
+    Bucket* b = find_or_make_bucket(s, *r, r->stage, &err);
+    if (err != GPSOC_OK) return err;
+    if (!b) { waiting.push_back(t); continue; }
+    int slot = -1;
+    for (size_t k = 0; k < b->slot.size(); ++k)
+      if (b->slot[k] < 0) { slot = (int)k; break; }
+    gpsoc_status st = load_slot(b, slot, *r);
+    if (st != GPSOC_OK) return st;
+    b->slot[slot] = (int64_t)t;
+  }
+  s->queue.swap(waiting);
+  // 3. every idle bucket that holds work starts its next round on its own stream
+  const int iters = s->opts.iters_per_step > 0 ? s->opts.iters_per_step : 32;
+  const int pairs = (iters + 1) / 2;
+  int n_busy = (int)s->queue.size();
+  for (Bucket* b : s->buckets) {
+    for (int64_t t : b->slot) n_busy += (t >= 0);
+    if (b->in_flight || bucket_empty(b)) continue;
+    const int k = (b->stage == 1) ? 1 : 0;
+    gpsoc_status st = (k == 1) ? build_graph<float>(b->p, 0, b->o) : build_graph<double>(b->p, 0, b->o);
+    if (st != GPSOC_OK) return st;
+    for (int r = 0; r < pairs; ++r) {
+      CK(cudaGraphLaunch(b->p->graph[k], b->p->stream));
+      b->p->launches += b->p->graph_kernels[k];
+    }
+    CK(cudaEventRecord(b->done, b->p->stream));
+    b->in_flight = true;
+    b->launched = ++s->rounds;
+  }
   if (busy) *busy = n_busy;
   return GPSOC_OK;
 }

@@ -132,3 +132,28 @@ def smooth_random_state(n, L, seed: int, width: float = 1.5) -> np.ndarray:
     X = mesh(n, L)
     env = np.exp(-sum(x * x for x in X) / (2 * width * width))
     return random_state(n, seed) * env[None]
+
+
+# grids of the served trace: (n, L) with their draw weights
+SERVE_GRIDS = [((64, 64), (12.0, 12.0)), ((128, 128), (12.0, 12.0)), ((256, 256), (12.0, 12.0)),
+               ((512, 512), (12.0, 12.0)), ((64, 64, 64), (8.0, 8.0, 8.0)), ((128, 128, 128), (8.0, 8.0, 8.0))]
+SERVE_WEIGHTS = [0.30, 0.25, 0.20, 0.10, 0.10, 0.05]
+
+
+def serve_trace(seed: int, count: int, rate: float):
+    """Served-trace requests: Poisson arrivals at `rate` per second (exponential
+    gaps), a grid drawn from SERVE_GRIDS by SERVE_WEIGHTS, parameters drawn as in
+    batch_params, and a guess seed.  Returns dicts sorted by arrival time."""
+    rng = SplitMix64(seed)
+    pars = batch_params(seed + 1, count)
+    cum = np.cumsum(SERVE_WEIGHTS)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        g = int(np.searchsorted(cum, rng.uniform() * cum[-1], side="right"))
+        g = min(g, len(SERVE_GRIDS) - 1)
+        n, L = SERVE_GRIDS[g]
+        out.append({"arrival": t, "n": n, "L": L, "params": pars[k], "guess_seed": seed_for(5, k),
+                    "vortex": bool(k % 2)})
+    return out

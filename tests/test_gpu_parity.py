@@ -283,10 +283,23 @@ def test_mixed_precision_ground_state_matches_oracle():
     ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10))
     with Problem(n, L, [par], trap=trap) as p:
         p.set_initial(psi0[None])
-        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1)[0]
+        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1, fp32_min_points=-1)[0]
         got = p.psi()[0]
     assert res["fp32_iters"] > 0 and res["fp64_iters"] > 0
     _assert_ground_state_parity(m, ref, res, got)
+
+
+def test_mixed_precision_skips_fp32_on_small_levels():
+    # MIXED keeps levels below fp32_min_points solve-points (default 65536) in FP64
+    n, L, par = (64, 64), (8.0, 8.0), (0.5, 0.5, 100.0, -1.0)
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    with Problem(n, L, [par] * 4) as p:
+        p.set_initial(np.stack([psi0] * 4))
+        small = p.solve(tol=1e-10, precision=1, fp32_min_points=4 * 64 * 64 + 1)
+        p.set_initial(np.stack([psi0] * 4))
+        large = p.solve(tol=1e-10, precision=1, fp32_min_points=4 * 64 * 64)
+    assert all(r["fp32_iters"] == 0 and r["status"] == "OK" for r in small)
+    assert all(r["fp32_iters"] > 0 and r["status"] == "OK" for r in large)
 
 
 def test_mixed_precision_radial_trap_invariants_match_oracle():
@@ -298,7 +311,7 @@ def test_mixed_precision_radial_trap_invariants_match_oracle():
     ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10))
     with Problem(n, L, [par]) as p:
         p.set_initial(psi0[None])
-        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1)[0]
+        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1, fp32_min_points=-1)[0]
     assert res["status"] == "OK"
     assert res["energy"] == pytest.approx(ref.energy, rel=1e-10)
     assert res["mu"] == pytest.approx(ref.mu, rel=1e-10)
@@ -314,7 +327,7 @@ def test_mixed_precision_cm_batch_matches_fp64():
     for prec in (0, 1):
         with Problem(n, L, pars, trap=trap) as p:
             p.set_initial(psis, level=1)
-            out[prec] = (p.solve(tol=1e-12, res_tol=2e-10, cm_levels=2, precision=prec), p.psi())
+            out[prec] = (p.solve(tol=1e-12, res_tol=2e-10, cm_levels=2, precision=prec, fp32_min_points=-1), p.psi())
     for k in range(2):
         r64, r32 = out[0][0][k], out[1][0][k]
         assert r64["status"] == "OK" and r32["status"] == "OK"

@@ -26,7 +26,7 @@ REQS = [((32, 32), (6.0, 6.0), (0.3, 0.5, 60.0, -1.0)),
         ((16, 16, 16), (5.0, 5.0, 5.0), (0.2, 0.4, 30.0, -2.0)),
         ((32, 32), (6.0, 6.0), (0.6, 0.1, 150.0, 4.0)),
         ((64, 64), (8.0, 8.0), (0.1, 0.3, 40.0, -3.0))]
-OPTS = dict(tol=1e-12, res_tol=2e-10)
+OPTS = dict(tol=1e-12, res_tol=2e-10, fp32_min_points=-1)   # FP32 stage on every bucket when mixed
 
 
 def _alone(n, L, par, psi0):
