@@ -71,17 +71,22 @@ __device__ __forceinline__ void spin_a(C1 p1, C2 p0, C3 pm, W& ar, W& ai) {
 }
 
 template <class W> __device__ __forceinline__ W rsqrt_w(W x);
-template <> __device__ __forceinline__ double rsqrt_w<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ double rsqrt_w<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_w<float>(float x) { return rsqrtf(x); }
 
-// write per-thread partial sums (working precision) as a deterministic FP64 block total
+// write per-thread partial sums (working precision) as a deterministic block total in FP64
+// (FP32 partials are added in double-float, which carries more bits than the partials hold)
 template <int K, class W>
 __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&slots)[K], const bool (&mx)[K],
                                                double* red, double* part, long long sbase_slot, int pmax, int blk) {
   double v[K];
+  if constexpr (sizeof(W) == 4 && K >= 2) {
+    block_reduce_df<K>(acc, v, red);     // FP32 partials: double-float sums on the FP32 pipes
+  } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
-  block_reduce<K>(v, red, mx);
+    for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
+    block_reduce<K>(v, red, mx);
+  }
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) part[(sbase_slot + slots[k]) * pmax + blk] = v[k];

@@ -274,6 +274,7 @@ ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   s.nsolve = p->batch;
   s.phase = phase;
   s.npts = g.npts;
+  s.inv_npts = 1.0 / (double)g.npts;
   s.dV = g.dV;
   s.norm_scale = p->d_scale;
   (void)level;
@@ -293,6 +294,7 @@ ScalarCtx scalar_ctx(gpsoc_problem* p, const Geo& g, const OptsDev& o, int flags
   c.dV = g.dV;
   c.opts = o;
   c.flags = flags;
+  c.inv_npts = 1.0 / (double)g.npts;
   return c;
 }
 

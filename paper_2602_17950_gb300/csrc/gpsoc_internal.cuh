@@ -124,6 +124,7 @@ struct ScalarCtx {
   double dV;
   OptsDev opts;
   int flags;            // 2 = count accepted steps as FP32 iterations
+  double inv_npts;      // 1 / npts
 };
 
 template <class T>
@@ -262,6 +263,76 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, co
     double acc = scratch[threadIdx.x];
     for (int w = 1; w < nw; ++w) acc += scratch[w * 16 + threadIdx.x];
     res[threadIdx.x] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = res[k];
+}
+
+// Double-float ("FP32 pair") arithmetic for the reductions of FP32 kernels: a
+// value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  Sums use
+// Knuth's TwoSum (an error-free transformation), so adding FP32 per-thread
+// partials this way is as accurate as FP64 adds while issuing on the FP32 pipes.
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum: a.hi + b.hi = s + e exactly
+  const float t = a.lo + b.lo + e;
+  const float h = s + t;                             // FastTwoSum(s, t): |s| >= |t|
+  DF r;
+  r.hi = h;
+  r.lo = t - (h - s);
+  return r;
+}
+__device__ __forceinline__ DF df_shfl_xor(DF a, int ofs) {
+  DF r;
+  r.hi = __shfl_xor_sync(0xffffffffu, a.hi, ofs);
+  r.lo = __shfl_xor_sync(0xffffffffu, a.lo, ofs);
+  return r;
+}
+
+// Block sums of FP32 per-thread partials in double-float, same fixed order and
+// same reduce-scatter scheme as block_reduce; the K totals are rounded to FP64
+// once at the end.  scratch: >= 16 * (blockDim.x / 32) + 16 doubles.
+template <int K>
+__device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)[K], double* scratch) {
+  static_assert(K >= 2 && K <= 16, "block_reduce_df handles 2..16 values");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();  // scratch may alias shared memory the caller used just before
+  constexpr int KP = (K <= 2) ? 2 : (K <= 4) ? 4 : (K <= 8) ? 8 : 16;
+  constexpr int LB = (KP == 2) ? 1 : (KP == 4) ? 2 : (KP == 8) ? 3 : 4;
+  DF x[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) { x[k].hi = (k < K) ? a[k] : 0.0f; x[k].lo = 0.0f; }
+#pragma unroll
+  for (int st = 0; st < LB; ++st) {
+    const int ofs = 1 << st, half = (KP / 2) >> st;
+    const bool up = (lane & ofs) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const DF keep = up ? x[i + half] : x[i];
+      const DF send = up ? x[i] : x[i + half];
+      x[i] = df_add(keep, df_shfl_xor(send, ofs));
+    }
+  }
+#pragma unroll
+  for (int ofs = KP; ofs < 32; ofs <<= 1) x[0] = df_add(x[0], df_shfl_xor(x[0], ofs));
+  int slot = 0;
+#pragma unroll
+  for (int b = 0; b < LB; ++b) slot |= ((lane >> b) & 1) << (LB - 1 - b);
+  float2* sc2 = reinterpret_cast<float2*>(scratch);
+  if (lane < KP) sc2[warp * 16 + slot] = make_float2(x[0].hi, x[0].lo);
+  __syncthreads();
+  double* res = scratch + 16 * nw;
+  if (threadIdx.x < K) {
+    const float2 f = sc2[threadIdx.x];
+    DF acc{f.x, f.y};
+    for (int w = 1; w < nw; ++w) {
+      const float2 g = sc2[w * 16 + threadIdx.x];
+      acc = df_add(acc, DF{g.x, g.y});
+    }
+    res[threadIdx.x] = (double)acc.hi + (double)acc.lo;
   }
   __syncthreads();
 #pragma unroll

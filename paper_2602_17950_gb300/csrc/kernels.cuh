@@ -33,6 +33,7 @@ struct ScalarArgs {
   int force;          // process every solve regardless of its active flag
   const double* thetas; int n_theta; double* model_out;
   int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
+  double inv_npts = 0.0;   // 1 / npts
 };
 
 enum ElemMode { EL_DIR = 0, EL_UPDATE, EL_MASS, EL_SCALE };

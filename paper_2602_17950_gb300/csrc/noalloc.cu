@@ -205,6 +205,7 @@ extern "C" gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpso
   x.nb_row = nb_row;
   x.nb_col = col_blocks_per_solve<double>(g, g.d - 1, batch);
   x.nsolve = batch; x.phase = PH_OBS; x.npts = g.npts; x.dV = g.dV; x.force = 1;
+  x.inv_npts = 1.0 / (double)g.npts;
   launch_scalar(x, st);
   k_gather_obs<<<(batch + 127) / 128, 128, 0, st>>>(sst, batch, dobs);
   e = cudaGetLastError();

@@ -25,7 +25,7 @@ __global__ void k_scalar(ScalarArgs A) {
   const int ph_ = A.phase;
   if (A.only >= 0 && s != A.only) return;
   if (ph_ != PH_INIT && ph_ != PH_NORM && !A.force && !S.active) return;
-  ScalarCtx X{A.st, A.phys, A.part, A.pmax, A.nb_row, A.nb_col, A.npts, A.dV, A.opts, A.flags};
+  ScalarCtx X{A.st, A.phys, A.part, A.pmax, A.nb_row, A.nb_col, A.npts, A.dV, A.opts, A.flags, A.inv_npts};
   switch (ph_) {
     case PH_INIT:
       if (threadIdx.x == 0) {
@@ -48,12 +48,16 @@ __global__ void k_scalar(ScalarArgs A) {
     case PH_STEP: sc_step(X, s, scratch); return;
     case PH_CLEAR: if (threadIdx.x == 0) S.pending = 0; return;
     case PH_MODEL: {
-      step_sums(X, s, scratch);
+      SolveState L;
+      if (threadIdx.x == 0) L = S;
+      PNorm pn;
+      step_sums(X, s, scratch, L, pn);
       if (threadIdx.x == 0) {
+        S = L;
         const PhysDev ph = A.phys[s];
         double* o = A.model_out + (long long)s * (2 + A.n_theta);
-        o[0] = S.a; o[1] = S.b;
-        for (int k = 0; k < A.n_theta; ++k) o[2 + k] = energy_change(S, ph.c0, ph.c1, A.thetas[k]);
+        o[0] = L.a; o[1] = L.b;
+        for (int k = 0; k < A.n_theta; ++k) o[2 + k] = energy_change(L, ph.c0, ph.c1, A.thetas[k]);
       }
       return;
     }
@@ -98,9 +102,14 @@ __global__ void k_elem(ElemArgs<T> A) {
         acc[3] += h.x * z.x + h.y * z.y;
       }
     }
-    double v[4] = {(double)acc[0], (double)acc[1], (double)acc[2], (double)acc[3]};
-    const bool mx[4] = {};
-    block_reduce<4>(v, scratch, mx);
+    double v[4];
+    if constexpr (sizeof(W) == 4) {
+      block_reduce_df<4>(acc, v, scratch);
+    } else {
+      for (int k = 0; k < 4; ++k) v[k] = (double)acc[k];
+      const bool mx[4] = {};
+      block_reduce<4>(v, scratch, mx);
+    }
     if (threadIdx.x == 0) {
       double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
       P[(long long)SL_DPHI * A.pmax] = v[0];

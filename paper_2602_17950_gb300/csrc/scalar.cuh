@@ -9,17 +9,22 @@
 
 namespace gpsoc {
 
-// K slot totals (sums over the nb block partials of solve s); every thread gets them
+// K slot totals (sums over the nb block partials of solve s); every thread gets them.
+// The K partials of a block index are loaded together (one memory round trip per
+// blockDim partials, not one per slot).
 template <int K>
 __device__ __forceinline__ void slot_totals(const ScalarCtx& X, int s, const int (&slots)[K], int nb, double (&v)[K],
                                             double* scratch) {
   const bool mx[K] = {};
+  const double* base = X.part + (long long)s * NSLOT * X.pmax;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double* p = X.part + ((long long)s * NSLOT + slots[k]) * X.pmax;
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(p + b);
-    v[k] = acc;
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = __ldcg(base + (long long)slots[k] * X.pmax + b);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += t[k];
   }
   block_reduce<K>(v, scratch, mx);
 }
@@ -39,18 +44,25 @@ __device__ __forceinline__ void deactivate(SolveState& S, int status) {
 }
 
 // E, mu (Eqs. energy, muphi), alpha_l (Eq. PreCnstAlpha), masses of the current iterate
-__device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratch) {
-  SolveState& S = X.st[s];
+// The solve state of a fused tail is copied to shared memory by the whole block
+// (one round of loads), updated there by thread 0, and copied back by the block:
+// thread 0 then never waits on a global-memory round trip per field, and the
+// copy holds no registers of the kernel it is fused into.
+__device__ __forceinline__ void state_load(SolveState& dst, const SolveState* src) {
+  static_assert(sizeof(SolveState) % 8 == 0, "state is copied in 8-byte words");
+  auto* d = reinterpret_cast<unsigned long long*>(&dst);
+  const auto* q = reinterpret_cast<const unsigned long long*>(src);
+  for (int i = threadIdx.x; i < (int)(sizeof(SolveState) / 8); i += blockDim.x) d[i] = q[i];
+}
+__device__ __forceinline__ void state_store(SolveState* dst, const SolveState& src) {
+  auto* d = reinterpret_cast<unsigned long long*>(dst);
+  const auto* q = reinterpret_cast<const unsigned long long*>(&src);
+  for (int i = threadIdx.x; i < (int)(sizeof(SolveState) / 8); i += blockDim.x) d[i] = q[i];
+}
+
+__device__ __forceinline__ void obs_update(const ScalarCtx& X, int s, SolveState& S, const double (&kin)[3],
+                                           const double (&v)[12], bool had_step, double dphi) {
   const PhysDev ph = X.phys[s];
-  double kin[3], v[12];
-  const int kslots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
-  slot_totals<3>(X, s, kslots, X.nb_col, kin, scratch);
-  const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
-  slot_totals<12>(X, s, slots, X.nb_row, v, scratch);
-  const bool had_step = S.pending != 0;
-  double dphi = 0.0;
-  if (had_step) dphi = slot_max(X, s, SL_DPHIINF, X.nb_row, scratch);
-  if (threadIdx.x != 0) return;
   const double dV = X.dV;
   S.Q = dV * v[0];
   S.rho2 = dV * v[1];
@@ -59,7 +71,7 @@ __device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratc
   S.mu = S.Q + ph.c0 * S.rho2 + ph.c1 * S.F2;
   double amax = 0.0;
   for (int c = 0; c < 3; ++c) {
-    S.alpha[c] = dV * (kin[c] / (double)X.npts + v[3 + c] + ph.c0 * v[6 + c]);
+    S.alpha[c] = dV * (kin[c] * X.inv_npts + v[3 + c] + ph.c0 * v[6 + c]);
     S.mass[c] = dV * v[9 + c];
     amax = fmax(amax, fabs(S.alpha[c]));
   }
@@ -69,6 +81,23 @@ __device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratc
   S.pending = 0;
   if (!isfinite(S.E) || !isfinite(S.mu) || !isfinite(S.alpha[0] + S.alpha[1] + S.alpha[2]))
     deactivate(S, GPSOC_ENONFINITE);
+}
+
+// E, mu (Eqs. energy, muphi), alpha_l (Eq. PreCnstAlpha), masses of the current iterate
+__device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratch) {
+  __shared__ SolveState sS;
+  state_load(sS, X.st + s);      // visible after the barrier that opens the first reduction
+  double kin[3], v[12];
+  const int kslots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
+  slot_totals<3>(X, s, kslots, X.nb_col, kin, scratch);
+  const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
+  slot_totals<12>(X, s, slots, X.nb_row, v, scratch);
+  const bool had_step = sS.pending != 0;
+  double dphi = 0.0;
+  if (had_step) dphi = slot_max(X, s, SL_DPHIINF, X.nb_row, scratch);
+  if (threadIdx.x == 0) obs_update(X, s, sS, kin, v, had_step, dphi);
+  __syncthreads();
+  state_store(X.st + s, sS);
 }
 
 constexpr int kStallWindow = 256;
@@ -142,16 +171,28 @@ __device__ __forceinline__ void sc_cproj(const ScalarCtx& X, int s, double* scra
   }
 }
 
-// E(cos t Phi + sin t P/||P||) - E(Phi) from the reduced integrals (unnormalised P):
-// quadratic part -s^2 Q + 2cs/|P| Re<H_lin Phi,P> + s^2/|P|^2 <H_lin P,P>, interaction
-// part from rho_t - rho = u rho_Phi + w1 R + w2 rho_P (u = -s^2, w1 = 2cs/|P|, w2 = s^2/|P|^2)
-// and the same for the spin density (Section 3.1, the explicit form of E(theta)).
-__device__ __forceinline__ double energy_change(const SolveState& S, double c0, double c1, double theta) {
-  const double nP2 = S.P2, nP = sqrt(nP2);
+// |P| and the reciprocals of |P| and |P|^2: one square root and one division
+// per step (FP64 square roots and divisions are long instruction sequences).
+struct PNorm {
+  double nP, inv_nP, inv_nP2;
+};
+__device__ __forceinline__ PNorm p_norm(double nP2) {
+  PNorm r;
+  r.inv_nP2 = 1.0 / nP2;
+  r.nP = sqrt(nP2);
+  r.inv_nP = r.nP * r.inv_nP2;
+  return r;
+}
+
+// E(cos t Phi + sin t P/||P||) - E(Phi) from the reduced integrals (unnormalised P),
+// given sn = sin t, cs = cos t: quadratic part -s^2 Q + 2cs/|P| Re<H_lin Phi,P> +
+// s^2/|P|^2 <H_lin P,P>, interaction part from rho_t - rho = u rho_Phi + w1 R + w2 rho_P
+// (u = -s^2, w1 = 2cs/|P|, w2 = s^2/|P|^2) and the same for the spin density
+// (Section 3.1, the explicit form of E(theta)).
+__device__ __forceinline__ double energy_change_sc(const SolveState& S, double c0, double c1, double sn, double cs,
+                                                   const PNorm& pn) {
   const double QFP = S.HPhiP - c0 * S.I[1] - c1 * S.J[1];
-  double sn, cs;
-  sincos(theta, &sn, &cs);
-  const double u = -sn * sn, w1 = 2.0 * cs * sn / nP, w2 = sn * sn / nP2;
+  const double u = -sn * sn, w1 = 2.0 * cs * sn * pn.inv_nP, w2 = sn * sn * pn.inv_nP2;
   const double quad = u * S.Q + w1 * QFP + w2 * S.HPP;
   const double* I = S.I;
   const double* J = S.J;
@@ -164,9 +205,15 @@ __device__ __forceinline__ double energy_change(const SolveState& S, double c0, 
   return quad + 0.5 * c0 * (2.0 * rl + rq) + 0.5 * c1 * (2.0 * fl + fq);
 }
 
-// gather the step-model sums of the P chain into the state; returns (a_n, b_n) (Eqs. an, bn)
-__device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scratch) {
-  SolveState& S = X.st[s];
+__device__ __forceinline__ double energy_change(const SolveState& S, double c0, double c1, double theta) {
+  double sn, cs;
+  sincos(theta, &sn, &cs);
+  return energy_change_sc(S, c0, c1, sn, cs, p_norm(S.P2));
+}
+
+// gather the step-model sums of the P chain into S (thread 0 holds the result);
+// a_n, b_n of Eqs. an, bn
+__device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scratch, SolveState& S, PNorm& pn) {
   double v[14];
   const int slots[14] = {SL_P2, SL_HPP, SL_HPHIP, SL_RPHI, SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,
                          SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP};
@@ -177,19 +224,16 @@ __device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scr
   for (int k = 0; k < 5; ++k) { S.I[k + 1] = dV * v[4 + k]; S.J[k + 1] = dV * v[9 + k]; }
   S.I[0] = S.rho2; S.J[0] = S.F2;
   const PhysDev ph = X.phys[s];
-  const double nP2 = S.P2;
+  pn = p_norm(S.P2);
   // density frozen at Phi^n in H_l(P^n)
-  S.a = -S.mu + (S.HPP + ph.c0 * S.I[2] + ph.c1 * S.J[2]) / nP2 + 2.0 * (ph.c0 * S.I[3] + ph.c1 * S.J[3]) / nP2;
-  S.b = 2.0 * S.HPhiP / sqrt(nP2);
+  S.a = -S.mu + (S.HPP + ph.c0 * S.I[2] + ph.c1 * S.J[2] + 2.0 * (ph.c0 * S.I[3] + ph.c1 * S.J[3])) * pn.inv_nP2;
+  S.b = 2.0 * S.HPhiP * pn.inv_nP;
 }
 
 // Algorithm 2: step size from the quadratic model, backtracking on the exact
 // energy change, update coefficients of Eqs. formula-pcg / update (applied by
-// the next iteration's first pass).
-__device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scratch) {
-  step_sums(X, s, scratch);
-  if (threadIdx.x != 0) return;
-  SolveState& S = X.st[s];
+// the next iteration's first pass).  Thread 0, on its copy S of the state.
+__device__ __forceinline__ void step_decide(const ScalarCtx& X, int s, SolveState& S, const PNorm& pn) {
   const PhysDev ph = X.phys[s];
   const OptsDev& O = X.opts;
   const double a = S.a, b = S.b;
@@ -208,9 +252,10 @@ __device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scrat
   }
   double theta = (a > 0.0 && b < 0.0) ? -b / (2.0 * a) : O.theta_trial;
   bool accepted = false;
-  double dE = 0.0;
+  double dE = 0.0, sn = 0.0, cs = 1.0;
   for (int h = 0; h <= O.max_halvings; ++h) {
-    dE = energy_change(S, ph.c0, ph.c1, theta);
+    sincos(theta, &sn, &cs);
+    dE = energy_change_sc(S, ph.c0, ph.c1, sn, cs, pn);
     if (dE < 0.0) { accepted = true; break; }
     theta *= O.sigma;
     S.halvings++;
@@ -220,21 +265,28 @@ __device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scrat
     else deactivate(S, GPSOC_ESTAGNATED);
     return;
   }
-  double sn, cs;
-  sincos(theta, &sn, &cs);
-  const double nP2 = S.P2, nP = sqrt(nP2);
   S.theta = theta;
   S.dE = dE;
   S.dE_last = dE;
-  const double sp = sn / nP;
+  const double sp = sn * pn.inv_nP;
   const double M = S.mass[0] + S.mass[1] + S.mass[2];
-  const double nrm2 = cs * cs * M + 2.0 * cs * sp * S.RPhi + sp * sp * nP2;
-  S.upd_c = cs; S.upd_s = sp; S.upd_scale = 1.0 / sqrt(nrm2);
+  const double nrm2 = cs * cs * M + 2.0 * cs * sp * S.RPhi + sp * sp * S.P2;
+  S.upd_c = cs; S.upd_s = sp; S.upd_scale = rsqrt(nrm2);
   S.pending = 1;
   S.iters++; S.total_iters++;
   if (X.flags & 2) S.fp32_iters++; else S.fp64_iters++;
   S.first = 0;
   S.s_prev = S.s_cur;
+}
+
+__device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scratch) {
+  __shared__ SolveState sS;
+  state_load(sS, X.st + s);      // visible after the barrier that opens the reduction
+  PNorm pn;
+  step_sums(X, s, scratch, sS, pn);
+  if (threadIdx.x == 0) step_decide(X, s, sS, pn);
+  __syncthreads();
+  state_store(X.st + s, sS);
 }
 
 }  // namespace gpsoc
