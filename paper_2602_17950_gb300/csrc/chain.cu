@@ -82,6 +82,8 @@ __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&sl
   double v[K];
   if constexpr (sizeof(W) == 4 && K >= 2) {
     block_reduce_df<K>(acc, v, red);     // FP32 partials: double-float sums on the FP32 pipes
+  } else if constexpr (sizeof(W) == 4) {
+    v[0] = block_reduce1_f(acc[0], mx[0], red);
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
@@ -126,12 +128,12 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
 
   if (MODE == ROW_FWD_PLAIN || MODE == ROW_FWD_UPD || MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE) {
     W acc[1] = {(W)0};
-    const W cproj = (W)S.cproj, mu = A.given_r ? (W)0 : (W)S.mu, beta = (W)S.beta;
-    const bool use_prev = (MODE == ROW_FWD_PROJ) && S.beta != 0.0;
+    const W cproj = pick<W>(S.cproj, S.fcproj), mu = A.given_r ? (W)0 : pick<W>(S.mu, S.fmu), beta = pick<W>(S.beta, S.fbeta);
+    const bool use_prev = (MODE == ROW_FWD_PROJ) && pick<W>(S.beta, S.fbeta) != (W)0;
     const bool upd = (MODE == ROW_FWD_UPD) && S.pending != 0;
-    const W uc = (W)S.upd_c, us = (W)S.upd_s, usc = (W)S.upd_scale;
-    const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
-    const W c0 = (W)ph.c0;
+    const W uc = pick<W>(S.upd_c, S.fupd_c), us = pick<W>(S.upd_s, S.fupd_s), usc = pick<W>(S.upd_scale, S.fupd_scale);
+    const W al[3] = {pick<W>(S.alpha[0], S.falpha[0]), pick<W>(S.alpha[1], S.falpha[1]), pick<W>(S.alpha[2], S.falpha[2])};
+    const W c0 = pick<W>(ph.c0, ph.fc0);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const long long off = rbase + e;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   else row_fft<C, true, 1>(buf0, buf1, 3 * R, NP, Lx, s_tw, ept);
 
   const W inv_n = (W)1 / (W)npts;
-  const W Om = (W)ph.Omega;
+  const W Om = pick<W>(ph.Omega, ph.fOmega);
   if (MODE == ROW_INV_PLAIN) {
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -244,8 +246,8 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     // z = P_V^{1/2} F^-1[...] (Eq. PreCondMix); reduce Re<r, z>, Re<r_prev, z>
     W acc[2] = {(W)0, (W)0};
     const bool use_prev = (A.in3 != nullptr) && !S.first;
-    const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
-    const W c0 = (W)ph.c0;
+    const W al[3] = {pick<W>(S.alpha[0], S.falpha[0]), pick<W>(S.alpha[1], S.falpha[1]), pick<W>(S.alpha[2], S.falpha[2])};
+    const W c0 = pick<W>(ph.c0, ph.fc0);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const int pos = r * NP + fft_pad(j);
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   }
 
   // ROW_INV_H / ROW_INV_P / ROW_INV_LIN: lin = F_x^-1(T')/npts - Omega x F_x^-1(G)/npts + V u
-  const W c0 = (W)ph.c0, c1 = (W)ph.c1;
+  const W c0 = pick<W>(ph.c0, ph.fc0), c1 = pick<W>(ph.c1, ph.fc1);
   W acc[13];
 #pragma unroll
   for (int k = 0; k < 13; ++k) acc[k] = (W)0;
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     const long long off = rbase + e;
     const long long row = off / nx;
     const int iy = (int)(row % ny), iz = (int)(row / ny);
-    const W x = (W)(-A.g.L[0]) + (W)j * (W)A.g.h[0];
+    const W x = coord<W>(A.g, 0, j);
     const W V = trap_value<W>(A.trap, A.g, j, iy, iz, off);
     C u[3];  // Phi for ROW_INV_H, P for ROW_INV_P / ROW_INV_LIN
     W lin_r[3], lin_i[3];
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const long long obase = (long long)o * na * ni + i0;
   const SolveState& S = A.st[s];
   const PhysDev ph = A.phys[s];
-  const double piA = A.g.piL[axis];
+  const W piA = geo_piL<W>(A.g, axis);
   const int nx = A.g.n[0];
   // smem index of element j of column t, component c: c * CS + t * NPL + pad(j)
   auto sidx = [&](int c, int t, int j) { return c * CS + t * NPL + fft_pad(j); };
@@ -474,8 +476,8 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   // inner index -> (kx [, ky]) wavenumbers (inputs are spectral along the faster axes)
   auto kinner = [&](int t, W& kx, W& ky) {
     const int ii = i0 + t;
-    if (axis == 1) { kx = wavenum<W>(ii, nx, A.g.piL[0]); ky = (W)0; }
-    else { kx = wavenum<W>(ii % nx, nx, A.g.piL[0]); ky = wavenum<W>(ii / nx, A.g.n[1], A.g.piL[1]); }
+    if (axis == 1) { kx = wavenum<W>(ii, nx, geo_piL<W>(A.g, 0)); ky = (W)0; }
+    else { kx = wavenum<W>(ii % nx, nx, geo_piL<W>(A.g, 0)); ky = wavenum<W>(ii / nx, A.g.n[1], geo_piL<W>(A.g, 1)); }
   };
 
   if (MODE == COL_YINV_H) {
@@ -496,8 +498,8 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       const int j = e / TC, t = e - j * TC;
       W kx, ky;
       kinner(t, kx, ky);
-      const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
-      const W rot = nfac * (W)ph.Omega * y * kx;
+      const W y = coord<W>(A.g, 1, j);
+      const W rot = nfac * pick<W>(ph.Omega, ph.fOmega) * y * kx;
       const long long gi = sbase + obase + (long long)j * ni + t;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -533,8 +535,8 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 
   W acc[3] = {(W)0, (W)0, (W)0};
   // pointwise in k: the kinetic + SOC symbol (H chains) or the kinetic preconditioner
-  const W al[3] = {(W)S.alpha[0], (W)S.alpha[1], (W)S.alpha[2]};
-  const W g = (W)ph.gamma;
+  const W al[3] = {pick<W>(S.alpha[0], S.falpha[0]), pick<W>(S.alpha[1], S.falpha[1]), pick<W>(S.alpha[2], S.falpha[2])};
+  const W g = pick<W>(ph.gamma, ph.fgamma);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
     const int i1 = sidx(0, t, j), i2 = sidx(1, t, j), i3 = sidx(2, t, j);
@@ -569,14 +571,14 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
 
   const W nrot = (W)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
-  const W Om = (W)ph.Omega;
+  const W Om = pick<W>(ph.Omega, ph.fOmega);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
     const long long gi = sbase + obase + (long long)j * ni + t;
     if (MODE == COL_YMID_H) {
       W kx, ky;
       kinner(t, kx, ky);
-      const W y = (W)(-A.g.L[1]) + (W)j * (W)A.g.h[1];
+      const W y = coord<W>(A.g, 1, j);
       const W rot = nrot * Om * y * kx;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

@@ -174,6 +174,9 @@ Geo make_geo(const gpsoc_problem* p, int level) {
     }
     g.log2n[i] = ilog2(g.n[i]);
     g.npts *= g.n[i];
+    g.fL[i] = (float)g.L[i];
+    g.fh[i] = (float)g.h[i];
+    g.fpiL[i] = (float)g.piL[i];
   }
   return g;
 }
@@ -184,6 +187,9 @@ TrapDev make_trap(const gpsoc_problem* p, int level) {
   t.quad = (p->trap.kind == GPSOC_TRAP_HARMONIC) ? 0.0 : p->trap.quad;
   t.quart = (p->trap.kind == GPSOC_TRAP_HARMONIC) ? 0.0 : p->trap.quart;
   t.userV = (level == 0) ? p->d_userV : nullptr;
+  for (int i = 0; i < 3; ++i) t.fhalf_g2[i] = (float)t.half_g2[i];
+  t.fquad = (float)t.quad;
+  t.fquart = (float)t.quart;
   return t;
 }
 
@@ -735,7 +741,7 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
   p->tmp_len = (size_t)batch * 64 + 4096;
   if (cudaMalloc(&p->d_tmp, sizeof(double) * p->tmp_len) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
   std::vector<PhysDev> ph(batch);
-  for (int b = 0; b < batch; ++b) ph[b] = PhysDev{params[b].Omega, params[b].gamma, params[b].beta0, params[b].beta1};
+  for (int b = 0; b < batch; ++b) ph[b] = make_phys(params[b].Omega, params[b].gamma, params[b].beta0, params[b].beta1);
   if (cudaMalloc(&p->d_phys, sizeof(PhysDev) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
   if (cudaMemcpy(p->d_phys, ph.data(), sizeof(PhysDev) * batch, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(GPSOC_ECUDA, "copy failed");
@@ -1012,7 +1018,7 @@ gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* t
   double* d_out = p->d_tmp + n_theta;
   if (n_theta) CK(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, p->stream));
   // cproj = 0 so that P is used as given
-  for (int i = 0; i < p->batch; ++i) { p->h_st[i].cproj = 0.0; p->h_st[i].beta = 0.0; }
+  for (int i = 0; i < p->batch; ++i) { p->h_st[i].cproj = 0.0; p->h_st[i].beta = 0.0; p->h_st[i].fcproj = 0.0f; p->h_st[i].fbeta = 0.0f; }
   CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
   ChainArgs<double> a;
   s = chain_args<double>(p, p->level, a);
@@ -1219,7 +1225,7 @@ gpsoc_status load_slot(Bucket* b, int s, const ServerReq& r) {
   const Geo g = make_geo(p, 0);
   const size_t off = (size_t)s * 3 * g.npts;
   CK(cudaMemcpyAsync(p->b64.Phi + off, r.psi.data(), sizeof(double2) * 3 * g.npts, cudaMemcpyHostToDevice, p->stream));
-  const PhysDev ph{r.par.Omega, r.par.gamma, r.par.beta0, r.par.beta1};
+  const PhysDev ph = make_phys(r.par.Omega, r.par.gamma, r.par.beta0, r.par.beta1);
   CK(cudaMemcpyAsync(p->d_phys + s, &ph, sizeof(PhysDev), cudaMemcpyHostToDevice, p->stream));
   ElemArgs<double> e = elem_args<double>(p, g, GATE_ALL);
   e.only = s;

@@ -44,15 +44,33 @@ struct Geo {
   double piL[3];    // pi / L per axis: wavenumber of index k is p * piL with p = k or k - n
   long long npts;   // points of one component
   double dV;        // h^d
+  float fL[3], fh[3], fpiL[3];   // FP32 copies for FP32 kernels (no per-thread FP64 conversions)
 };
 
 struct TrapDev {
   double half_g2[3];   // g_i^2 / 2
   double quad, quart;
   const double* userV; // npts doubles of the current level or nullptr
+  float fhalf_g2[3], fquad, fquart;   // FP32 copies
 };
 
-struct PhysDev { double Omega, gamma, c0, c1; };
+struct PhysDev {
+  double Omega, gamma, c0, c1;
+  float fOmega, fgamma, fc0, fc1;    // FP32 copies
+};
+
+__host__ __device__ inline PhysDev make_phys(double Omega, double gamma, double c0, double c1) {
+  PhysDev p;
+  p.Omega = Omega; p.gamma = gamma; p.c0 = c0; p.c1 = c1;
+  p.fOmega = (float)Omega; p.fgamma = (float)gamma; p.fc0 = (float)c0; p.fc1 = (float)c1;
+  return p;
+}
+
+// the copy of a scalar in the working precision W: FP32 kernels read the FP32
+// copy (an FP64-to-FP32 conversion issues on the FP64 pipe, 1/64 of the FP32 rate)
+template <class W> __device__ __forceinline__ W pick(double d, float f) {
+  if constexpr (sizeof(W) == 4) return f; else return d;
+}
 
 // Per-solve scalar state of the PCG iteration (device resident).
 struct SolveState {
@@ -78,7 +96,15 @@ struct SolveState {
   double a, b, theta, dE, dE_last;
   double upd_c, upd_s, upd_scale;
   double E_win;     // FP32 phase: energy when the stall window opened
+  // FP32 copies of the scalars the array passes read (refreshed by mirror32)
+  float fmu, fbeta, fcproj, fupd_c, fupd_s, fupd_scale, falpha[3], fpad;
 };
+
+__device__ __forceinline__ void mirror32(SolveState& S) {
+  S.fmu = (float)S.mu; S.fbeta = (float)S.beta; S.fcproj = (float)S.cproj;
+  S.fupd_c = (float)S.upd_c; S.fupd_s = (float)S.upd_s; S.fupd_scale = (float)S.upd_scale;
+  for (int c = 0; c < 3; ++c) S.falpha[c] = (float)S.alpha[c];
+}
 
 struct OptsDev {
   int stop;
@@ -176,24 +202,29 @@ __device__ __forceinline__ bool last_block(unsigned* cnt, int s, int bps, int* f
 // wavenumber v_p = pi p / L of FFT index k on an axis of n points (Section 3.2),
 // evaluated in the working precision W of the kernel
 template <class W>
-__device__ __forceinline__ W wavenum(int k, int n, double piL) {
+__device__ __forceinline__ W wavenum(int k, int n, W piL) {
   const int p = (k < (n >> 1)) ? k : k - n;
-  return (W)p * (W)piL;
+  return (W)p * piL;
+}
+template <class W> __device__ __forceinline__ W geo_piL(const Geo& g, int a) { return pick<W>(g.piL[a], g.fpiL[a]); }
+// physical coordinate -L + i h of grid index i on axis a
+template <class W> __device__ __forceinline__ W coord(const Geo& g, int a, int i) {
+  return -pick<W>(g.L[a], g.fL[a]) + (W)i * pick<W>(g.h[a], g.fh[a]);
 }
 
 // trapping potential at grid point (ix, iy, iz) in the working precision W
 template <class W>
 __device__ __forceinline__ W trap_value(const TrapDev& t, const Geo& g, int ix, int iy, int iz, long long idx) {
-  const W x = (W)(-g.L[0]) + (W)ix * (W)g.h[0];
-  const W y = (W)(-g.L[1]) + (W)iy * (W)g.h[1];
-  W v = (W)t.half_g2[0] * x * x + (W)t.half_g2[1] * y * y;
+  const W x = coord<W>(g, 0, ix);
+  const W y = coord<W>(g, 1, iy);
+  W v = pick<W>(t.half_g2[0], t.fhalf_g2[0]) * x * x + pick<W>(t.half_g2[1], t.fhalf_g2[1]) * y * y;
   W r2 = x * x + y * y;
   if (g.d == 3) {
-    const W z = (W)(-g.L[2]) + (W)iz * (W)g.h[2];
-    v += (W)t.half_g2[2] * z * z;
+    const W z = coord<W>(g, 2, iz);
+    v += pick<W>(t.half_g2[2], t.fhalf_g2[2]) * z * z;
     r2 += z * z;
   }
-  v += (W)t.quad * r2 + (W)t.quart * r2 * r2;
+  v += pick<W>(t.quad, t.fquad) * r2 + pick<W>(t.quart, t.fquart) * r2 * r2;
   if (t.userV) v += (W)t.userV[idx];
   return v;
 }
@@ -290,6 +321,33 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int ofs) {
   r.hi = __shfl_xor_sync(0xffffffffu, a.hi, ofs);
   r.lo = __shfl_xor_sync(0xffffffffu, a.lo, ofs);
   return r;
+}
+
+// One FP32 block total (a sum in double-float, or a max in FP32, which is exact),
+// rounded to FP64 once.  scratch: >= blockDim.x / 32 + 1 doubles.
+__device__ __forceinline__ double block_reduce1_f(float a, bool is_max, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();  // scratch may alias shared memory the caller used just before
+  DF x{a, 0.0f};
+#pragma unroll
+  for (int ofs = 16; ofs > 0; ofs >>= 1) {
+    const DF o = df_shfl_xor(x, ofs);
+    if (is_max) x.hi = fmaxf(x.hi, o.hi);
+    else x = df_add(x, o);
+  }
+  float2* sc2 = reinterpret_cast<float2*>(scratch);
+  if (lane == 0) sc2[warp] = make_float2(x.hi, is_max ? 0.0f : x.lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DF acc{sc2[0].x, sc2[0].y};
+    for (int w = 1; w < nw; ++w) {
+      if (is_max) acc.hi = fmaxf(acc.hi, sc2[w].x);
+      else acc = df_add(acc, DF{sc2[w].x, sc2[w].y});
+    }
+    scratch[nw] = (double)acc.hi + (double)acc.lo;
+  }
+  __syncthreads();
+  return scratch[nw];
 }
 
 // Block sums of FP32 per-thread partials in double-float, same fixed order and

@@ -145,7 +145,7 @@ extern "C" gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpso
       if (!std::isfinite(q.Omega) || !std::isfinite(q.gamma) || !std::isfinite(q.beta0) || !std::isfinite(q.beta1)) {
         return GPSOC_EINVAL;
       }
-      phs[k] = PhysDev{q.Omega, q.gamma, q.beta0, q.beta1};
+      phs[k] = make_phys(q.Omega, q.gamma, q.beta0, q.beta1);
     }
     e = cudaMemcpyAsync(ph + b0, phs, sizeof(PhysDev) * nb, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return GPSOC_ECUDA;

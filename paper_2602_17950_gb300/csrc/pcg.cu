@@ -32,6 +32,7 @@ __global__ void k_scalar(ScalarArgs A) {
         S.active = 1; S.status = GPSOC_OK; S.iters = 0; S.first = 1; S.reset = 0; S.pending = 0;
         S.dE_last = nan(""); S.dphi_inf = nan(""); S.E_win = INFINITY; S.it_win = 0;
         if (A.flags & 1) { S.total_iters = 0; S.beta_resets = 0; S.halvings = 0; S.fp32_iters = 0; S.fp64_iters = 0; }
+        mirror32(S);
       }
       return;
     case PH_NORM: {
@@ -84,8 +85,8 @@ __global__ void k_elem(ElemArgs<T> A) {
   if (MODE == EL_DIR) {
     // D = -z + beta P_prev (Section 3.1) is not stored: reduce Re<D, Phi>, Re<H Phi, D>,
     // Re<z, Phi>, Re<H Phi, z> for the projection and the sign test of Algorithm 2 Step 2
-    const W beta = (W)S.beta;
-    const bool use_prev = S.beta != 0.0;
+    const W beta = pick<W>(S.beta, S.fbeta);
+    const bool use_prev = pick<W>(S.beta, S.fbeta) != (W)0;
     W acc[4] = {(W)0, (W)0, (W)0, (W)0};
     for (long long e = threadIdx.x; e < per; e += blockDim.x) {
 #pragma unroll
@@ -123,7 +124,7 @@ __global__ void k_elem(ElemArgs<T> A) {
   W acc = (W)0;
   if (MODE == EL_UPDATE) {
     // Phi <- (cos t Phi + sin t P/||P||) / norm (Eqs. formula-pcg, update); reduce max |dPhi|^2
-    const W cs = (W)S.upd_c, sp = (W)S.upd_s, sc = (W)S.upd_scale;
+    const W cs = pick<W>(S.upd_c, S.fupd_c), sp = pick<W>(S.upd_s, S.fupd_s), sc = pick<W>(S.upd_scale, S.fupd_scale);
     for (long long e = threadIdx.x; e < per; e += blockDim.x) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {

@@ -81,6 +81,7 @@ __device__ __forceinline__ void obs_update(const ScalarCtx& X, int s, SolveState
   S.pending = 0;
   if (!isfinite(S.E) || !isfinite(S.mu) || !isfinite(S.alpha[0] + S.alpha[1] + S.alpha[2]))
     deactivate(S, GPSOC_ENONFINITE);
+  mirror32(S);
 }
 
 // E, mu (Eqs. energy, muphi), alpha_l (Eq. PreCnstAlpha), masses of the current iterate
@@ -148,6 +149,7 @@ __device__ __forceinline__ void sc_beta(const ScalarCtx& X, int s, double* scrat
     if (!(beta > 0.0)) beta = 0.0;   // max(beta, 0), NaN -> 0
   }
   S.beta = beta;
+  S.fbeta = (float)beta;
 }
 
 // Tangent projection coefficient c = Re<D, Phi> (Eq. formula-project), and
@@ -169,6 +171,8 @@ __device__ __forceinline__ void sc_cproj(const ScalarCtx& X, int s, double* scra
   } else {
     S.cproj = cD;
   }
+  S.fbeta = (float)S.beta;
+  S.fcproj = (float)S.cproj;
 }
 
 // |P| and the reciprocals of |P| and |P|^2: one square root and one division
@@ -284,7 +288,10 @@ __device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scrat
   state_load(sS, X.st + s);      // visible after the barrier that opens the reduction
   PNorm pn;
   step_sums(X, s, scratch, sS, pn);
-  if (threadIdx.x == 0) step_decide(X, s, sS, pn);
+  if (threadIdx.x == 0) {
+    step_decide(X, s, sS, pn);
+    mirror32(sS);
+  }
   __syncthreads();
   state_store(X.st + s, sS);
 }
