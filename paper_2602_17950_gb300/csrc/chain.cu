@@ -59,7 +59,7 @@ __device__ __forceinline__ void row_fft(C* buf0, C* buf1, int nlines, int NP, in
 
 // odd padded length of a column line in shared memory (distinct banks for
 // consecutive columns)
-__host__ __device__ __forceinline__ int col_line_len(int n) { return fft_padded_len(n) | 1; }
+template <class C> __host__ __device__ __forceinline__ int col_line_len(int n) { return fft_padded_len<C>(n) | 1; }
 
 // spin terms shared by the pointwise epilogues (working precision W):
 //   a = conj(p0) p1 + conj(pm) p0  so that F_-/sqrt2 = a, F_+/sqrt2 = conj(a),
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   C* s_tw = (C*)smem_raw;
   C* buf0 = s_tw + nx;
   const int per = R * nx;             // elements of one component in the tile
-  const int NP = fft_padded_len(nx), CP = R * NP;   // padded line length, component stride in smem
+  const int NP = fft_padded_len<C>(nx), CP = R * NP;   // padded line length, component stride in smem
   constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
   C* buf1 = buf0 + 3 * CP;
   double* red = (double*)(buf1 + (two ? 3 * CP : 0));
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
       const long long off = rbase + e;
-      const int pos = r * NP + fft_pad(j);
+      const int pos = r * NP + fft_pad<C>(j);
       if (MODE == ROW_FWD_PLAIN) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) buf0[c * CP + pos] = A.in0[sbase + c * npts + off];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     __syncthreads();
     row_fft<C, false, 1>(buf0, buf1, 3 * R, NP, Lx, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
-      const int pos = (e / nx) * NP + fft_pad(e % nx);
+      const int pos = (e / nx) * NP + fft_pad<C>(e % nx);
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + rbase + e] = buf0[c * CP + pos];
     }
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   // ---------------------------------------------------------------- inverse passes
   // natural order in shared memory, inverse transform in place
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
-    const int pos = (e / nx) * NP + fft_pad(e % nx);
+    const int pos = (e / nx) * NP + fft_pad<C>(e % nx);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       buf0[c * CP + pos] = A.in0[sbase + c * npts + rbase + e];
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
-      const int pos = r * NP + fft_pad(j);
+      const int pos = r * NP + fft_pad<C>(j);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const C v = buf0[c * CP + pos];
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     const W c0 = pick<W>(ph.c0, ph.fc0);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int r = e / nx, j = e - r * nx;
-      const int pos = r * NP + fft_pad(j);
+      const int pos = r * NP + fft_pad<C>(j);
       const long long off = rbase + e;
       W rho = (W)0;
 #pragma unroll
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   for (int k = 0; k < 13; ++k) acc[k] = (W)0;
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int r = e / nx, j = e - r * nx;
-    const int pos = r * NP + fft_pad(j);
+    const int pos = r * NP + fft_pad<C>(j);
     const long long off = rbase + e;
     const long long row = off / nx;
     const int iy = (int)(row % ny), iz = (int)(row / ny);
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   C* s_tw = (C*)smem_raw;
   C* buf = s_tw + na;
   const int per = na * TC;
-  const int NPL = col_line_len(na);            // odd padded line length
+  const int NPL = col_line_len<C>(na);            // odd padded line length
   const int CS = TC * NPL;                     // component stride in smem
   C* buf2 = buf + 3 * CS;            // second 3-component tile (YMID_H, YINV_H)
   double* red = (double*)(buf2 + 3 * CS);
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const W piA = geo_piL<W>(A.g, axis);
   const int nx = A.g.n[0];
   // smem index of element j of column t, component c: c * CS + t * NPL + pad(j)
-  auto sidx = [&](int c, int t, int j) { return c * CS + t * NPL + fft_pad(j); };
+  auto sidx = [&](int c, int t, int j) { return c * CS + t * NPL + fft_pad<C>(j); };
 
   // load the in0 tile (and in1 for YINV_H) in natural order; global reads coalesced over t
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -669,14 +669,14 @@ static size_t row_smem(const Geo& g, int mode, int nsolve) {
   const int per = R * g.n[0];
   const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
   (void)per;
-  const int CP = R * fft_padded_len(g.n[0]);
+  const int CP = R * fft_padded_len<C>(g.n[0]);
   return sizeof(C) * (g.n[0] + 3 * CP * (two ? 2 : 1)) + kRedDoubles * sizeof(double);
 }
 
 template <class T>
 static size_t col_smem(const Geo& g, int axis, int nsolve) {
   using C = cx_t<T>;
-  const int CS = col_line_len(g.n[axis]) * col_tc<T>(g, axis, nsolve);
+  const int CS = col_line_len<C>(g.n[axis]) * col_tc<T>(g, axis, nsolve);
   return sizeof(C) * (g.n[axis] + 6 * CS) + kRedDoubles * sizeof(double);
 }
 

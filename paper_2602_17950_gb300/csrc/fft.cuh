@@ -10,17 +10,20 @@
 // output q to x[(g / Ns) Ns R + k + q Ns].  Every pass reads all values into
 // registers, synchronises, then writes: the transform runs in place.
 //
-// Lines are padded in shared memory, element e at e + (e >> 3), which keeps the
-// strided writes of the early passes free of bank conflicts for 8- and 16-byte
-// complex values.  tw holds W_N^m = exp(-2 pi i m / N) for m < N.
+// Lines are padded in shared memory, element e at e + (e >> 4) for 8-byte and
+// e + (e >> 3) for 16-byte complex values: the contiguous reads of every pass
+// and the strided writes of the first pass then avoid bank conflicts.  tw holds W_N^m = exp(-2 pi i m / N) for m < N.
 #pragma once
 
 #include "gpsoc_internal.cuh"
 
 namespace gpsoc {
 
-__host__ __device__ __forceinline__ int fft_pad(int e) { return e + (e >> 3); }
-__host__ __device__ __forceinline__ int fft_padded_len(int n) { return n + (n >> 3); }
+// one gap per 16 elements for 8-byte complex values (a half-warp's 16 consecutive
+// elements fill one 128-byte wavefront), one per 8 for 16-byte values
+template <class C> constexpr int kPadShift = (sizeof(C) == 8) ? 4 : 3;
+template <class C> __host__ __device__ __forceinline__ int fft_pad(int e) { return e + (e >> kPadShift<C>); }
+template <class C> __host__ __device__ __forceinline__ int fft_padded_len(int n) { return n + (n >> kPadShift<C>); }
 
 template <class C> __device__ __forceinline__ C cmul_conj_if(C a, C w, bool conj) {
   if (conj) w.y = -w.y;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void stockham_pass(C* const (&lines)[NI], const bool 
     for (int u = 0; u < PER; ++u) {
       const int g = g0 + u * (N / E);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[it][u * R + r] = lines[it][fft_pad(g + r * NR) * es];
+      for (int r = 0; r < R; ++r) v[it][u * R + r] = lines[it][fft_pad<C>(g + r * NR) * es];
     }
   }
   __syncthreads();
@@ -126,7 +129,7 @@ __device__ __forceinline__ void stockham_pass(C* const (&lines)[NI], const bool 
       dftR<C, INV, R, E>(v[it], u * R);
       const int ob = (g / Ns) * Ns * R + k;
 #pragma unroll
-      for (int q = 0; q < R; ++q) lines[it][fft_pad(ob + q * Ns) * es] = v[it][u * R + q];
+      for (int q = 0; q < R; ++q) lines[it][fft_pad<C>(ob + q * Ns) * es] = v[it][u * R + q];
     }
   }
   __syncthreads();
