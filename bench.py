@@ -269,33 +269,38 @@ def run_ours(args, rank, world, local_rank):
         e2e.append(time.perf_counter() - t0)
         ok = ok and r["status"] == "OK"
 
-    # per-kernel durations (CUDA events on the solver's stream) on every level's grid
+    # per-kernel durations (CUDA events on the solver's stream) on every level's grid, in
+    # each precision the solve used there (FP32 and FP64 iterations counted per level)
     last = results[-1]
+    fp32_lv = last.get("level_fp32_iters", [0] * LEVELS)
     prof = {}
     for lev in range(LEVELS):
         n = tuple(k >> (LEVELS - 1 - lev) for k in N_FINE)
-        with Problem(n, L_BOX, [PAR]) as pl:
-            pl.set_initial(si.gaussian_guess(n, L_BOX, si.seed_for(2, rank), vortex=True)[None], level=0)
-            prof[n[0]] = pl.profile(iters=20, precision=prec, tol=TOL)
+        its32 = fp32_lv[lev]
+        its64 = last["level_iters"][lev] - its32
+        for pr, its in ((1, its32), (0, its64)):
+            if its <= 0:
+                continue
+            with Problem(n, L_BOX, [PAR]) as pl:
+                pl.set_initial(si.gaussian_guess(n, L_BOX, si.seed_for(2, rank), vortex=True)[None], level=0)
+                prof[(n[0], pr)] = (its, pl.profile(iters=20, precision=pr, tol=TOL))
     fp64_peak, fp32_peak = probe_peaks()
     prob.close()
     if rank != 0:
         return None
 
-    # dominant (kernel, level): largest share of the solve time = iterations x duration
-    elem = 8 if prec == 1 else 16
+    # dominant (kernel, level, precision): largest share of the solve time = iterations x duration
     shares = {}
-    for lev, its in enumerate(last["level_iters"]):
-        n = N_FINE[0] >> (LEVELS - 1 - lev)
-        for name, ms in prof[n]:
-            shares[(name, n)] = shares.get((name, n), 0.0) + its * ms
+    for (n, pr), (its, pl_ms) in prof.items():
+        for name, ms in pl_ms:
+            shares[(name, n, pr)] = shares.get((name, n, pr), 0.0) + its * ms
     total_share = sum(shares.values())
-    (dom_name, dom_n), _ = max(shares.items(), key=lambda kv: kv[1])
-    dom_ms = statistics.mean([ms for name, ms in prof[dom_n] if name == dom_name])
+    (dom_name, dom_n, dom_pr), _ = max(shares.items(), key=lambda kv: kv[1])
+    dom_ms = statistics.mean([ms for name, ms in prof[(dom_n, dom_pr)][1] if name == dom_name])
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else 6800.0
-    if prec == 1:
-        by = kernel_bytes(dom_name, (dom_n, dom_n), elem)
+    if dom_pr == 1:
+        by = kernel_bytes(dom_name, (dom_n, dom_n), 8)
         achieved = by / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": f"{dom_name} @ {dom_n}^2 (FP32)", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
@@ -307,7 +312,7 @@ def run_ours(args, rank, world, local_rank):
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
                 "peak_source": "FP64 FMA-chain probe gpsoc_probe_peaks, this run (of measured)",
                 "algorithmic_flops_per_launch": fl}
-    roof.update({"ms_per_launch": dom_ms, "share_of_solve": shares[(dom_name, dom_n)] / total_share})
+    roof.update({"ms_per_launch": dom_ms, "share_of_solve": shares[(dom_name, dom_n, dom_pr)] / total_share})
     ms_per_step = max_total_ms / args.steps
     out = {
         "metric": METRIC, "value": whole_job_rate(world, args.steps, max_total_ms), "unit": "solves/s",
@@ -321,9 +326,10 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fp64_plain": fp64,
         "roofline": roof,
-        "kernels_us_per_iteration": {str(n): {k: round(v * 1e3, 2) for k, v in pr} for n, pr in prof.items()},
+        "kernels_us_per_iteration": {f"{n}_{'fp32' if pr else 'fp64'}": {k: round(v * 1e3, 2) for k, v in pl_ms}
+                                     for (n, pr), (_, pl_ms) in prof.items()},
         "solve": {"status_ok": ok, "energy": last["energy"], "mu": last["mu"], "iters_total": last["total_iters"],
-                  "level_iters": last["level_iters"], "fp32_iters": last["fp32_iters"],
+                  "level_iters": last["level_iters"], "level_fp32_iters": fp32_lv, "fp32_iters": last["fp32_iters"],
                   "fp64_iters": last["fp64_iters"], "beta_resets": last["beta_resets"]},
         "e2e": {"value": world / statistics.mean(e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h_in.numpy().nbytes), "d2h_bytes_per_step": int(h_out.numpy().nbytes)},

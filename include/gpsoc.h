@@ -118,7 +118,8 @@ typedef struct {
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;
  * res_inf = max_l ||r_l||_inf of that iterate; dE_last = energy change of the
  * last accepted step; level_iters[k] = iterations on multigrid level k
- * (k = 0 the coarsest, at most 8 levels). */
+ * (k = 0 the coarsest, at most 8 levels), level_fp32_iters[k] = those of them
+ * taken in FP32 arrays (GPSOC_MIXED). */
 typedef struct {
   int status;            /* gpsoc_status of this solve */
   int iters;             /* iterations on the finest level */
@@ -127,6 +128,7 @@ typedef struct {
   int beta_resets, halvings, fp32_iters, fp64_iters;
   double energy, mu, mass[3], res_inf, dE_last;
   int level_iters[8];
+  int level_fp32_iters[8];
 } gpsoc_result;
 
 typedef struct gpsoc_problem gpsoc_problem;

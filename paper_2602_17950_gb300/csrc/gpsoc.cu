@@ -126,6 +126,7 @@ struct gpsoc_problem {
   Tracker* tr = nullptr;        // active tracker while enqueueing
   std::vector<std::string> prof_names;
   std::vector<std::vector<int>> level_iters;   // per solve, iterations per level of the last solve
+  std::vector<std::vector<int>> level_fp32;    // per solve, FP32 iterations per level of the last solve
 };
 
 namespace {
@@ -631,7 +632,10 @@ void fill_results(const gpsoc_problem* p, gpsoc_result* r, int levels) {
   for (int i = 0; i < p->batch; ++i) {
     const SolveState& S = p->h_st[i];
     gpsoc_result& o = r[i];
-    for (int k = 0; k < 8; ++k) o.level_iters[k] = (i < (int)p->level_iters.size() && k < (int)p->level_iters[i].size()) ? p->level_iters[i][k] : 0;
+    for (int k = 0; k < 8; ++k) {
+      o.level_iters[k] = (i < (int)p->level_iters.size() && k < (int)p->level_iters[i].size()) ? p->level_iters[i][k] : 0;
+      o.level_fp32_iters[k] = (i < (int)p->level_fp32.size() && k < (int)p->level_fp32[i].size()) ? p->level_fp32[i][k] : 0;
+    }
     o.status = S.status;
     if (S.status == GPSOC_OK && S.active) o.status = GPSOC_ENOTCONV;
     o.iters = S.iters;
@@ -870,7 +874,8 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
   const int check = opts->check_every > 0 ? opts->check_every : 16;
   gpsoc_status s = GPSOC_OK;
   p->level_iters.assign(p->batch, std::vector<int>());
-  std::vector<int> done(p->batch, 0);
+  p->level_fp32.assign(p->batch, std::vector<int>());
+  std::vector<int> done(p->batch, 0), done32(p->batch, 0);
   for (int lev = levels - 1; lev >= 0; --lev) {
     if (lev < p->level) {
       s = prolong_impl(p, lev + 1);
@@ -881,7 +886,9 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
     if (s != GPSOC_OK) return s;
     for (int i = 0; i < p->batch; ++i) {
       p->level_iters[i].push_back(p->h_st[i].total_iters - done[i]);
+      p->level_fp32[i].push_back(p->h_st[i].fp32_iters - done32[i]);
       done[i] = p->h_st[i].total_iters;
+      done32[i] = p->h_st[i].fp32_iters;
     }
   }
   s = sync_state(p);
@@ -917,6 +924,7 @@ gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   s = sync_state(p);
   if (s != GPSOC_OK) return s;
   p->level_iters.assign(p->batch, std::vector<int>());
+  p->level_fp32.assign(p->batch, std::vector<int>());
   if (results) fill_results(p, results, 1);
   return GPSOC_OK;
 }
@@ -1416,6 +1424,7 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
       o.res_inf = S.res_inf;
       o.dE_last = S.dE_last;
       o.level_iters[0] = o.total_iters;
+      o.level_fp32_iters[0] = r->fp32_iters;
       r->stage = 3;
     }
   }

@@ -53,14 +53,15 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("total_iters", C.c_int), ("levels", C.c_int),
                 ("beta_resets", C.c_int), ("halvings", C.c_int), ("fp32_iters", C.c_int), ("fp64_iters", C.c_int),
                 ("energy", C.c_double), ("mu", C.c_double), ("mass", C.c_double * 3), ("res_inf", C.c_double),
-                ("dE_last", C.c_double), ("level_iters", C.c_int * 8)]
+                ("dE_last", C.c_double), ("level_iters", C.c_int * 8), ("level_fp32_iters", C.c_int * 8)]
 
     def as_dict(self):
         return {"status": status_name(self.status), "iters": self.iters, "total_iters": self.total_iters,
                 "levels": self.levels, "beta_resets": self.beta_resets, "halvings": self.halvings,
                 "fp32_iters": self.fp32_iters, "fp64_iters": self.fp64_iters, "energy": self.energy,
                 "mu": self.mu, "mass": list(self.mass), "res_inf": self.res_inf, "dE_last": self.dE_last,
-                "level_iters": list(self.level_iters[:max(self.levels, 1)])}
+                "level_iters": list(self.level_iters[:max(self.levels, 1)]),
+                "level_fp32_iters": list(self.level_fp32_iters[:max(self.levels, 1)])}
 
 
 class ServerOpts(C.Structure):
