@@ -367,7 +367,16 @@ def batch_case(args):
         its = [r["total_iters"] for r in res]
         out[name] = {"seconds": dt, "solves_per_s": B / dt, "converged": ok,
                      "iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)),
-                     "energies": [round(r["energy"], 10) for r in res[:4]]}
+                     "fp32_iters_mean": float(np.mean([r["fp32_iters"] for r in res])),
+                     "energies": [r["energy"] for r in res]}
+    if "fp64" in out and "mixed" in out:
+        d = [abs(a - b) / abs(b) for a, b in zip(out["mixed"]["energies"], out["fp64"]["energies"])]
+        out["mixed"]["energy_rel_diff_vs_fp64"] = {"max": max(d), "same_minimum_1e-8": sum(x < 1e-8 for x in d),
+                                                   "lower": sum(a < b for a, b in zip(out["mixed"]["energies"],
+                                                                                      out["fp64"]["energies"]))}
+    for name in ("fp64", "mixed"):
+        if name in out:
+            out[name]["energies"] = [round(e, 10) for e in out[name]["energies"][:4]]
     print(json.dumps(out))
 
 
@@ -454,7 +463,82 @@ def serve_case(args):
                 d = [abs(a["energy"] - b["energy"]) / abs(b["energy"]) for a, b in zip(rs, ref)
                      if a["status"] == "OK" and b["status"] == "OK"]
                 out[name]["energy_rel_diff_vs_plain_max"] = float(max(d)) if d else None
+                out[name]["same_minimum_as_plain_1e-8"] = int(sum(x < 1e-8 for x in d))
+                out[name]["lower_energy_than_plain"] = int(sum(a["energy"] < b["energy"] - 1e-8 * abs(b["energy"])
+                                                               for a, b in zip(rs, ref)))
                 out[name]["speedup_vs_plain"] = out[name]["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
+    print(json.dumps(out))
+
+
+def case1(args):
+    """The small plain-PCG workload: 64^2 on [-8,8]^2, harmonic trap, Omega = 0.5,
+    gamma = 0.5, beta0 = 100, beta1 = -1, seeded Gaussian components of mass 1/3,
+    stop |dE| < 1e-12; GPU FP64 (and mixed with an FP32 phase forced) against the
+    CPU oracle on the same input."""
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    build()
+    n, L, par = (64, 64), (8.0, 8.0), (0.5, 0.5, 100.0, -1.0)
+    psi = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    out = {"case1": "64^2 on [-8,8]^2, harmonic trap, Omega=0.5, gamma=0.5, beta0=100, beta1=-1, stop |dE|<1e-12"}
+    for name, kw in (("fp64", dict(precision=0)), ("mixed_forced", dict(precision=1, fp32_min_points=-1))):
+        with Problem(n, L, [par]) as p:
+            p.set_initial(psi[None])
+            p.solve(tol=TOL, **kw)                       # warm-up (graphs, twiddles)
+            p.set_initial(psi[None])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = p.solve(tol=TOL, **kw)[0]
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "status": r["status"], "energy": r["energy"], "mu": r["mu"],
+                     "iters": r["total_iters"], "fp32_iters": r["fp32_iters"]}
+    if not args.no_cpu:
+        from oracle.model import Grid, Model, Trap
+        from oracle.pcg import Options, pcg
+        m = Model(Grid(n, L), Trap(), Omega=par[0], gamma=par[1], c0=par[2], c1=par[3])
+        t0 = time.perf_counter()
+        ref = pcg(m, psi, Options(tol=TOL))
+        dt = time.perf_counter() - t0
+        out["oracle_cpu"] = {"seconds": dt, "cores": 1, "energy": ref.energy, "iters": ref.iters}
+        for name in ("fp64", "mixed_forced"):
+            out[name]["energy_rel_diff_vs_oracle"] = abs(out[name]["energy"] - ref.energy) / abs(ref.energy)
+    print(json.dumps(out))
+
+
+def case3d(args):
+    """The 3D mixed-precision workload: 128^3 on [-8,8]^3, trap (x^2+y^2+4z^2)/2 + 0.1 r^4,
+    Omega = 1.2, gamma = 1, beta0 = 500, beta1 = -2, seeded vortex-phase guess, stop
+    |dE| < 1e-10; mixed precision and plain FP64, one solve each (wall clock around the
+    solve call, device synchronised)."""
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    build()
+    n, L = (args.n3d,) * 3, (8.0, 8.0, 8.0)
+    trap = {"kind": 1, "g": (1.0, 1.0, 2.0), "quad": 0.0, "quart": 0.1}
+    par = (1.2, 1.0, 500.0, -2.0)
+    psi = si.gaussian_guess(n, L, si.seed_for(4, 0), vortex=True)
+    out = {"case3d": f"{n[0]}^3 on [-8,8]^3, trap (x^2+y^2+4z^2)/2 + 0.1 r^4, Omega=1.2, gamma=1, "
+                     f"beta0=500, beta1=-2, stop |dE|<1e-10, max_iter {args.max_iter}"}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        if name not in args.arms3d.split(","):
+            continue
+        with Problem(n, L, [par], trap=trap) as p:
+            p.set_initial(psi[None])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = p.solve(raise_on_error=False, tol=1e-10, precision=prec, max_iter=args.max_iter, check_every=64)[0]
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            prof = p.profile(iters=10, precision=prec, tol=1e-10)
+        out[name] = {"seconds": dt, "solves_per_s": 1.0 / dt, "status": r["status"], "energy": r["energy"],
+                     "mu": r["mu"], "iters": r["total_iters"], "fp32_iters": r["fp32_iters"],
+                     "fp64_iters": r["fp64_iters"], "iteration_us": round(sum(v for _, v in prof) * 1e3, 1),
+                     "us_per_launch": {k: round(v * 1e3, 1) for k, v in prof}}
+    if "mixed" in out and "fp64" in out:
+        out["energy_rel_diff"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"]) / abs(out["fp64"]["energy"])
     print(json.dumps(out))
 
 
@@ -510,7 +594,17 @@ def main():
     ap.add_argument("--hbm-budget", type=float, default=120e9, help="device bytes the server may use")
     ap.add_argument("--slots", type=int, default=16, help="solves per server bucket")
     ap.add_argument("--arms", default="served_mixed,served_fp64,plain_fp64", help="arms of --serve-case")
+    ap.add_argument("--case1", action="store_true", help="the small 64^2 plain-PCG workload vs the oracle")
+    ap.add_argument("--case3d", action="store_true", help="the 3D mixed-precision workload (128^3)")
+    ap.add_argument("--n3d", type=int, default=128, help="grid points per axis of --case3d")
+    ap.add_argument("--arms3d", default="mixed,fp64", help="arms of --case3d")
     args = ap.parse_args()
+    if args.case1:
+        case1(args)
+        return
+    if args.case3d:
+        case3d(args)
+        return
     if args.serve_case:
         serve_case(args)
         return
