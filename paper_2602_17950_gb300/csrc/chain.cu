@@ -1,7 +1,7 @@
 // Spectral passes of the Hamiltonian and preconditioner chains.
 //
 // A d-dimensional transform is a sequence of 1-D axis passes; each pass loads
-// a tile into shared memory, runs radix-2 FFTs there and stores back with
+// a tile into shared memory, runs Stockham FFTs there and stores back with
 // coalesced accesses.  Row passes (x, contiguous) take R whole rows of all
 // three components; column passes (y or z, strided) take a tile of TC
 // consecutive inner indices across the whole axis for all three components,
@@ -26,9 +26,11 @@ static constexpr int kThreads = 384;
 // reduction scratch (doubles) behind the tiles: block_reduce needs 16 per warp + 16
 static constexpr int kRedDoubles = 16 * (kThreads / 32) + 16;
 
+// twiddle table in shared memory, padded like the lines (the strided twiddle
+// reads of the later passes then spread over more banks)
 template <class T>
 __device__ __forceinline__ void load_tw(cx_t<T>* s_tw, const cx_t<T>* tw, int n) {
-  for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[k] = tw[k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[fft_pad<cx_t<T>>(k)] = tw[k];
 }
 
 // Row tiles: nlines lines of padded length NP; thread -> (line q, group g0), E
@@ -50,16 +52,31 @@ __device__ __forceinline__ void row_fft_e(C* buf0, C* buf1, int nlines, int NP, 
   }
 }
 
-template <class C, bool INV, int NI>
+// R16: the kernel may run radix-16 passes (FP32 column passes only: the code path
+// sets the register allocation of the whole kernel, and FP64 or two-line row
+// tiles would lose occupancy to it)
+template <class C, bool INV, int NI, bool R16 = false>
 __device__ __forceinline__ void row_fft(C* buf0, C* buf1, int nlines, int NP, int L, const C* tw, int ept) {
+  if constexpr (R16 && sizeof(C) == 8) {
+    if (ept == 16) { row_fft_e<C, INV, NI, 16>(buf0, buf1, nlines, NP, L, tw); return; }
+  }
   if (ept == 8) row_fft_e<C, INV, NI, 8>(buf0, buf1, nlines, NP, L, tw);
   else if (ept == 4) row_fft_e<C, INV, NI, 4>(buf0, buf1, nlines, NP, L, tw);
   else row_fft_e<C, INV, NI, 2>(buf0, buf1, nlines, NP, L, tw);
 }
 
-// odd padded length of a column line in shared memory (distinct banks for
-// consecutive columns)
-template <class C> __host__ __device__ __forceinline__ int col_line_len(int n) { return fft_padded_len<C>(n) | 1; }
+// padded length of a column line in shared memory
+template <class C> __host__ __device__ __forceinline__ int col_line_len(int n, int tc) {
+  // tiles are loaded with consecutive threads on consecutive columns, then on
+  // consecutive rows: S complex values fill a 128-byte wavefront, so the line
+  // stride is made S / tc modulo S (tc < S) or odd (tc >= S), which puts the
+  // values one half-warp (FP32) or quarter-warp (FP64) touches on distinct banks
+  constexpr int S = (sizeof(C) == 8) ? 16 : 8;
+  const int base = fft_padded_len<C>(n);
+  if (tc >= S) return base | 1;
+  const int want = S / tc;
+  return base + ((want - base % S) + S) % S;
+}
 
 // spin terms shared by the pointwise epilogues (working precision W):
 //   a = conj(p0) p1 + conj(pm) p0  so that F_-/sqrt2 = a, F_+/sqrt2 = conj(a),
@@ -112,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   const int rb = blockIdx.x % bps;
   if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   C* s_tw = (C*)smem_raw;
-  C* buf0 = s_tw + nx;
+  C* buf0 = s_tw + fft_padded_len<C>(nx);
   const int per = R * nx;             // elements of one component in the tile
   const int NP = fft_padded_len<C>(nx), CP = R * NP;   // padded line length, component stride in smem
   constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
@@ -403,9 +420,10 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
 // ============================================================== column passes (y or z axis)
 // Tile: inner indices [i0, i0 + TC) of the axis-`axis` lines at outer index o, all
 // three components.  Shared memory holds every (component, column) line
-// contiguously, line (c, t) at (c TC + t) NPL with an odd padded length NPL, so
-// the transforms run exactly as in the row passes and the transposing accesses
-// (consecutive threads on consecutive columns) fall on distinct banks.
+// contiguously, line (c, t) at (c TC + t) NPL with the padded length NPL of
+// col_line_len, so the transforms run exactly as in the row passes and the
+// transposing accesses (consecutive threads on consecutive columns) fall on
+// distinct banks.
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int TC, int ept) {
   using C = cx_t<T>;
@@ -423,9 +441,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const int o = tb / tpo;
   const int i0 = (tb % tpo) * TC;
   C* s_tw = (C*)smem_raw;
-  C* buf = s_tw + na;
+  C* buf = s_tw + fft_padded_len<C>(na);
   const int per = na * TC;
-  const int NPL = col_line_len<C>(na);            // odd padded line length
+  const int NPL = col_line_len<C>(na, TC);        // padded line length
   const int CS = TC * NPL;                     // component stride in smem
   C* buf2 = buf + 3 * CS;            // second 3-component tile (YMID_H, YINV_H)
   double* red = (double*)(buf2 + 3 * CS);
@@ -451,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   __syncthreads();
 
   if (MODE == COL_FWD) {
-    row_fft<C, false, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, false, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
 #pragma unroll
@@ -460,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     return;
   }
   if (MODE == COL_INV) {
-    row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, true, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
     const W sc = (W)A.scale;
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
@@ -482,8 +500,8 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 
   if (MODE == COL_YINV_H) {
     // buf: C -> F_y^-1 C;  buf2: A -> F_y A, times v_y, F_y^-1 -> G
-    row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
-    row_fft<C, false, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, true, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, false, 1, true>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
       const W vy = wavenum<W>(j, na, piA);
@@ -491,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       for (int c = 0; c < 3; ++c) buf2[sidx(c, t, j)] = cscale(buf2[sidx(c, t, j)], vy);
     }
     __syncthreads();
-    row_fft<C, true, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, true, 1, true>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     const W nfac = (W)A.g.n[1] * (W)A.g.n[2];  // ny * nz
     const W nz = (W)A.g.n[2];
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   }
 
   // forward transform along the axis: natural-order spectrum in buf
-  row_fft<C, false, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+  row_fft<C, false, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
 
   if (MODE == COL_YMID_H) {
     // G_c = F_y^-1[v_y F_y A_c] for the three components at once (buf2)
@@ -525,7 +543,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       for (int c = 0; c < 3; ++c) buf2[sidx(c, t, j)] = cscale(buf[sidx(c, t, j)], vy);
     }
     __syncthreads();
-    row_fft<C, true, 1>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
+    row_fft<C, true, 1, true>(buf2, buf2, 3 * TC, NPL, La, s_tw, ept);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
       const int j = e / TC, t = e - j * TC;
 #pragma unroll
@@ -568,7 +586,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     }
   }
   __syncthreads();
-  row_fft<C, true, 1>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+  row_fft<C, true, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
 
   const W nrot = (W)A.g.n[1];  // 2D: T' = F_y^-1[M F_y A] + ny Omega y v_x A
   const W Om = pick<W>(ph.Omega, ph.fOmega);
@@ -628,12 +646,15 @@ int col_tc(const Geo& g, int axis, int nsolve) {
   return tc;
 }
 
-// elements per thread of the FFT passes: 8 (radix-8 passes) unless the tile
-// would then have fewer than 128 threads, in which case 4 or 2 (more threads,
-// more passes); and the matching thread count (multiple of 32, >= 64)
-static int pick_ept(int work /* complex elements of the three components */) {
-  int e = 8;
-  while (e > 2 && work / e < 128) e >>= 1;
+// elements per thread of the FFT passes: 16 (radix-16 passes, FP32 column passes) or 8,
+// unless the tile would then have fewer than 128 threads or a line is shorter,
+// in which case fewer (more threads, more passes); and the matching thread
+// count (multiple of 32, >= 64)
+template <class T>
+static int pick_ept(int work /* complex elements of the three components */, int n /* line length */,
+                    bool r16 = true) {
+  int e = (sizeof(T) == 4 && r16) ? 16 : 8;
+  while (e > 2 && (work / e < 128 || e > n)) e >>= 1;
   return e;
 }
 static int round_threads(int t) {
@@ -645,7 +666,7 @@ template <class T>
 static void col_cfg(const Geo& g, int axis, int nsolve, int& tc, int& ept, int& threads) {
   tc = col_tc<T>(g, axis, nsolve);
   const int work = 3 * tc * g.n[axis];
-  ept = pick_ept(work);
+  ept = pick_ept<T>(work, g.n[axis]);
   threads = round_threads(work / ept);
 }
 
@@ -670,14 +691,15 @@ static size_t row_smem(const Geo& g, int mode, int nsolve) {
   const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
   (void)per;
   const int CP = R * fft_padded_len<C>(g.n[0]);
-  return sizeof(C) * (g.n[0] + 3 * CP * (two ? 2 : 1)) + kRedDoubles * sizeof(double);
+  return sizeof(C) * (fft_padded_len<C>(g.n[0]) + 3 * CP * (two ? 2 : 1)) + kRedDoubles * sizeof(double);
 }
 
 template <class T>
 static size_t col_smem(const Geo& g, int axis, int nsolve) {
   using C = cx_t<T>;
-  const int CS = col_line_len<C>(g.n[axis]) * col_tc<T>(g, axis, nsolve);
-  return sizeof(C) * (g.n[axis] + 6 * CS) + kRedDoubles * sizeof(double);
+  const int tc = col_tc<T>(g, axis, nsolve);
+  const int CS = col_line_len<C>(g.n[axis], tc) * tc;
+  return sizeof(C) * (fft_padded_len<C>(g.n[axis]) + 6 * CS) + kRedDoubles * sizeof(double);
 }
 
 template <class T, int MODE>
@@ -685,7 +707,7 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int R = row_rows_per_block<T>(a.g, a.nsolve);
   const int nb = row_blocks_per_solve<T>(a.g, a.nsolve) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE, a.nsolve);
-  const int ept = pick_ept(3 * R * a.g.n[0]);
+  const int ept = pick_ept<T>(3 * R * a.g.n[0], a.g.n[0], false);
   k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
 }
 

@@ -1,5 +1,5 @@
-// Shared-memory Stockham FFTs, radix 8 (plus one radix-2 or radix-4 pass when
-// log2 N is not a multiple of 3), natural order in and out.
+// Shared-memory Stockham FFTs, radix 16 or 8 (plus one smaller pass when log2 N
+// is not a multiple of 4 or 3), natural order in and out.
 //
 // Transform convention (Section 3.2): forward X_k = sum_m x_m exp(-2 pi i k m / N),
 // inverse with exp(+...) and no 1/N (callers fold the 1/N into their epilogues).
@@ -12,7 +12,8 @@
 //
 // Lines are padded in shared memory, element e at e + (e >> 4) for 8-byte and
 // e + (e >> 3) for 16-byte complex values: the contiguous reads of every pass
-// and the strided writes of the first pass then avoid bank conflicts.  tw holds W_N^m = exp(-2 pi i m / N) for m < N.
+// and the strided writes of the first pass then avoid bank conflicts.  tw holds
+// W_N^m = exp(-2 pi i m / N) for m < N at the padded index fft_pad(m).
 #pragma once
 
 #include "gpsoc_internal.cuh"
@@ -77,9 +78,55 @@ template <class C, bool INV> __device__ __forceinline__ void dft8(C (&v)[8]) {
   v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
 }
 
-// DFT of radix R on the R values starting at v[off] (R in {2, 4, 8})
+// v * exp(-i a) (forward) or v * exp(+i a) (inverse) for a constant angle with
+// cos a = c, sin a = s
+template <class C, bool INV, class R> __device__ __forceinline__ C rot_const(C v, R c, R s) {
+  C r;
+  if (INV) { r.x = v.x * c - v.y * s; r.y = v.y * c + v.x * s; }
+  else { r.x = v.x * c + v.y * s; r.y = v.y * c - v.x * s; }
+  return r;
+}
+
+// 16-point DFT in place: four 4-point DFTs over n1 (stride 4), the twiddles
+// W_16^(n2 k1), four 4-point DFTs over n2; output k = k1 + 4 k2 in natural order
+template <class C, bool INV> __device__ __forceinline__ void dft16(C (&v)[16]) {
+  using R = decltype(v[0].x);
+  const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+  C a[4][4];   // a[n2][k1]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
+    dft4<C, INV>(x0, x1, x2, x3);
+    a[n2][0] = x0; a[n2][1] = x1; a[n2][2] = x2; a[n2][3] = x3;
+  }
+  // W_16^m for m = n2 k1: 1, 2, 3 (n2 = 1); 2, 4, 6 (n2 = 2); 3, 6, 9 (n2 = 3)
+  a[1][1] = rot_const<C, INV>(a[1][1], c1, s1);
+  a[1][2] = rot_const<C, INV>(a[1][2], h, h);
+  a[1][3] = rot_const<C, INV>(a[1][3], s1, c1);
+  a[2][1] = rot_const<C, INV>(a[2][1], h, h);
+  a[2][2] = mul_mi<C, INV>(a[2][2]);
+  a[2][3] = rot_const<C, INV>(a[2][3], -h, h);
+  a[3][1] = rot_const<C, INV>(a[3][1], s1, c1);
+  a[3][2] = rot_const<C, INV>(a[3][2], -h, h);
+  a[3][3] = rot_const<C, INV>(a[3][3], -c1, -s1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C y0 = a[0][k1], y1 = a[1][k1], y2 = a[2][k1], y3 = a[3][k1];
+    dft4<C, INV>(y0, y1, y2, y3);
+    v[k1] = y0; v[k1 + 4] = y1; v[k1 + 8] = y2; v[k1 + 12] = y3;
+  }
+}
+
+// DFT of radix R on the R values starting at v[off] (R in {2, 4, 8, 16})
 template <class C, bool INV, int R, int E> __device__ __forceinline__ void dftR(C (&v)[E], int off) {
-  if constexpr (R == 8) {
+  if constexpr (R == 16) {
+    C w[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) w[r] = v[off + r];
+    dft16<C, INV>(w);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[off + r] = w[r];
+  } else if constexpr (R == 8) {
     C w[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) w[r] = v[off + r];
@@ -124,7 +171,7 @@ __device__ __forceinline__ void stockham_pass(C* const (&lines)[NI], const bool 
       if (k != 0) {
         const int step = k * (N / (Ns * R));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[it][u * R + r] = cmul_conj_if(v[it][u * R + r], tw[r * step], INV);
+        for (int r = 1; r < R; ++r) v[it][u * R + r] = cmul_conj_if(v[it][u * R + r], tw[fft_pad<C>(r * step)], INV);
       }
       dftR<C, INV, R, E>(v[it], u * R);
       const int ob = (g / Ns) * Ns * R + k;
@@ -135,8 +182,8 @@ __device__ __forceinline__ void stockham_pass(C* const (&lines)[NI], const bool 
   __syncthreads();
 }
 
-// Full transform of length N = 2^L (L >= 3) for the NI lines of this thread, E
-// elements per thread and pass (E in {2, 4, 8}: radix-E passes plus one smaller
+// Full transform of length N = 2^L (N >= E) for the NI lines of this thread, E
+// elements per thread and pass (E in {2, 4, 8, 16}: radix-E passes plus one smaller
 // pass when log2 N is not a multiple of log2 E).  Threads with g0 >= N/E (or
 // inactive items) only join the barriers.
 template <class C, bool INV, int E, int NI>
@@ -147,10 +194,13 @@ __device__ __forceinline__ void stockham_fft(C* const (&lines)[NI], const bool (
 #pragma unroll
   for (int it = 0; it < NI; ++it) active[it] = active_in[it] && g0 < (N / E);
   int Ns = 1;
-  constexpr int LE = (E == 8) ? 3 : (E == 4) ? 2 : 1;
+  constexpr int LE = (E == 16) ? 4 : (E == 8) ? 3 : (E == 4) ? 2 : 1;
   const int rem = L % LE;
   if (rem == 1) { stockham_pass<C, INV, 2, E, NI>(lines, active, g0, es, N, Ns, tw); Ns *= 2; }
   else if (rem == 2) { stockham_pass<C, INV, 4, E, NI>(lines, active, g0, es, N, Ns, tw); Ns *= 4; }
+  else if constexpr (E == 16) {
+    if (rem == 3) { stockham_pass<C, INV, 8, E, NI>(lines, active, g0, es, N, Ns, tw); Ns *= 8; }
+  }
   for (int p = 0; p < L / LE; ++p) { stockham_pass<C, INV, E, E, NI>(lines, active, g0, es, N, Ns, tw); Ns *= E; }
 }
 
