@@ -26,11 +26,17 @@ static constexpr int kThreads = 384;
 // reduction scratch (doubles) behind the tiles: block_reduce needs 16 per warp + 16
 static constexpr int kRedDoubles = 16 * (kThreads / 32) + 16;
 
-// twiddle table in shared memory, padded like the lines (the strided twiddle
-// reads of the later passes then spread over more banks)
+// Twiddle table in shared memory for transforms with E elements per thread:
+// entry (r, j) = W_n^(r j), r < E, j < n/E, at the padded index fft_pad(r n/E + j).
+// The last pass (radix E, Ns = n/E) reads j = k for consecutive groups k:
+// consecutive addresses; earlier passes read j = k n/(Ns E) for few distinct k.
 template <class T>
-__device__ __forceinline__ void load_tw(cx_t<T>* s_tw, const cx_t<T>* tw, int n) {
-  for (int k = threadIdx.x; k < n; k += blockDim.x) s_tw[fft_pad<cx_t<T>>(k)] = tw[k];
+__device__ __forceinline__ void load_tw(cx_t<T>* s_tw, const cx_t<T>* tw, int n, int ept) {
+  const int lc = __ffs(n / ept) - 1;   // log2(n / E): n and E are powers of two
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i >> lc, j = i & ((1 << lc) - 1);
+    s_tw[fft_pad<cx_t<T>>(i)] = tw[r * j];
+  }
 }
 
 // Row tiles: nlines lines of padded length NP; thread -> (line q, group g0), E
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
   C* buf1 = buf0 + 3 * CP;
   double* red = (double*)(buf1 + (two ? 3 * CP : 0));
-  load_tw<T>(s_tw, A.tw[0], nx);
+  load_tw<T>(s_tw, A.tw[0], nx, ept);
   const long long sbase = (long long)s * 3 * npts;
   const long long rbase = (long long)rb * R * nx;   // offset of the tile inside a component
   const long long sslot = (long long)s * NSLOT;
@@ -447,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const int CS = TC * NPL;                     // component stride in smem
   C* buf2 = buf + 3 * CS;            // second 3-component tile (YMID_H, YINV_H)
   double* red = (double*)(buf2 + 3 * CS);
-  load_tw<T>(s_tw, A.tw[axis], na);
+  load_tw<T>(s_tw, A.tw[axis], na, ept);
   const long long sbase = (long long)s * 3 * npts;
   const long long obase = (long long)o * na * ni + i0;
   const SolveState& S = A.st[s];

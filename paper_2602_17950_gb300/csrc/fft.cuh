@@ -13,7 +13,8 @@
 // Lines are padded in shared memory, element e at e + (e >> 4) for 8-byte and
 // e + (e >> 3) for 16-byte complex values: the contiguous reads of every pass
 // and the strided writes of the first pass then avoid bank conflicts.  tw holds
-// W_N^m = exp(-2 pi i m / N) for m < N at the padded index fft_pad(m).
+// W_N^(r j) = exp(-2 pi i r j / N) for r < E, j < N/E at the padded index
+// fft_pad(r N/E + j) (E = elements per thread, the radix of the last pass).
 #pragma once
 
 #include "gpsoc_internal.cuh"
@@ -169,9 +170,12 @@ __device__ __forceinline__ void stockham_pass(C* const (&lines)[NI], const bool 
       const int g = g0 + u * (N / E);
       const int k = g % Ns;
       if (k != 0) {
-        const int step = k * (N / (Ns * R));
+        // W_N^(r k N / (Ns R)): entry (r, k N / (Ns R)) of the table (R = E here:
+        // only the first pass, with k = 0, can have a smaller radix)
+        const int j = k * (N / (Ns * R));
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[it][u * R + r] = cmul_conj_if(v[it][u * R + r], tw[fft_pad<C>(r * step)], INV);
+        for (int r = 1; r < R; ++r)
+          v[it][u * R + r] = cmul_conj_if(v[it][u * R + r], tw[fft_pad<C>(r * (N / E) + j)], INV);
       }
       dftR<C, INV, R, E>(v[it], u * R);
       const int ob = (g / Ns) * Ns * R + k;
