@@ -52,6 +52,10 @@ typedef enum {
 enum { GPSOC_TRAP_HARMONIC = 0, GPSOC_TRAP_HARMONIC_QUARTIC = 1, GPSOC_TRAP_USER = 2 };
 enum { GPSOC_FP64 = 0, GPSOC_MIXED = 1 };
 enum { GPSOC_STOP_DPHI = 1, GPSOC_STOP_RES = 2, GPSOC_STOP_ENERGY = 3 };
+/* Preconditioner of the PCG (Section 3.4): the combined P_C = P_V^(1/2) P_Delta P_V^(1/2)
+ * (Eq. PreCondMix), the kinetic P_Delta alone (Eq. PreCondKin), the potential P_V alone
+ * (Eq. PreCondPot), or none (z = r). */
+enum { GPSOC_PRECOND_COMBINED = 0, GPSOC_PRECOND_KINETIC = 1, GPSOC_PRECOND_POTENTIAL = 2, GPSOC_PRECOND_NONE = 3 };
 
 /* Grid of Section 3.2.  dim = 2 or 3; n[i], L[i] for x, y(, z). */
 typedef struct {
@@ -100,7 +104,8 @@ typedef struct {
  *   fp32_min_points  GPSOC_MIXED only: a level (or server bucket) whose solves x
  *                grid points fall below this runs in FP64 alone, since FP32
  *                arrays save little on work that is bound by launch latency;
- *                0 selects 65536, a negative value gives every level an FP32 phase. */
+ *                0 selects 65536, a negative value gives every level an FP32 phase.
+ *   precond      GPSOC_PRECOND_* (0 = the combined preconditioner). */
 typedef struct {
   int precision;
   int stop;
@@ -113,6 +118,7 @@ typedef struct {
   int check_every;
   double fp32_switch;
   int fp32_min_points;
+  int precond;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;

@@ -196,6 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
           buf0[c * CP + pos] = p;
         }
       } else {  // ROW_FWD_PRE: r = H Phi - mu Phi, then P_V^{1/2} r (Eq. PreCondPot)
+        const int pk = A.sc.opts.precond;
+        const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
         C f[3], h[3];
         W rho = (W)0;
 #pragma unroll
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
           acc[0] = fmax(acc[0], sqrt(rr.x * rr.x + rr.y * rr.y));
           W den = al[c] + V + c0 * rho;
           den = fmax(den, (W)1e-12 * al[c]);
-          const W sc = rsqrt_w<W>(den);
+          const W sc = use_pv ? rsqrt_w<W>(den) : (W)1;
           buf0[c * CP + pos] = mk<C>(rr.x * sc, rr.y * sc);
         }
       }
@@ -269,6 +271,8 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
     // z = P_V^{1/2} F^-1[...] (Eq. PreCondMix); reduce Re<r, z>, Re<r_prev, z>
     W acc[2] = {(W)0, (W)0};
     const bool use_prev = (A.in3 != nullptr) && !S.first;
+    const int pk = A.sc.opts.precond;
+    const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
     const W al[3] = {pick<W>(S.alpha[0], S.falpha[0]), pick<W>(S.alpha[1], S.falpha[1]), pick<W>(S.alpha[2], S.falpha[2])};
     const W c0 = pick<W>(ph.c0, ph.fc0);
     for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
       for (int c = 0; c < 3; ++c) {
         W den = al[c] + V + c0 * rho;
         den = fmax(den, (W)1e-12 * al[c]);
-        const W sc = inv_n * rsqrt_w<W>(den);
+        const W sc = use_pv ? inv_n * rsqrt_w<W>(den) : inv_n;
         const C v = buf0[c * CP + pos];
         const C z = mk<C>(v.x * sc, v.y * sc);
         A.out0[sbase + c * npts + off] = z;
@@ -561,6 +565,7 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   // pointwise in k: the kinetic + SOC symbol (H chains) or the kinetic preconditioner
   const W al[3] = {pick<W>(S.alpha[0], S.falpha[0]), pick<W>(S.alpha[1], S.falpha[1]), pick<W>(S.alpha[2], S.falpha[2])};
   const W g = pick<W>(ph.gamma, ph.fgamma);
+  const bool use_pd = (A.sc.opts.precond == GPSOC_PRECOND_COMBINED || A.sc.opts.precond == GPSOC_PRECOND_KINETIC);
   for (int e = threadIdx.x; e < per; e += blockDim.x) {
     const int j = e / TC, t = e - j * TC;
     const int i1 = sidx(0, t, j), i2 = sidx(1, t, j), i3 = sidx(2, t, j);
@@ -570,9 +575,13 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
     else kz = wavenum<W>(j, na, piA);
     const W k2h = (W)0.5 * (kx * kx + ky * ky + kz * kz);
     if (MODE == COL_MID_PRE) {
-      buf[i1] = cscale(buf[i1], (W)1 / (al[0] + k2h));
-      buf[i2] = cscale(buf[i2], (W)1 / (al[1] + k2h));
-      buf[i3] = cscale(buf[i3], (W)1 / (al[2] + k2h));
+      // P_Delta (Eq. PreCondKin); the potential-only and no-preconditioner variants keep
+      // the coefficients (the transform pair is then the identity up to rounding)
+      if (use_pd) {
+        buf[i1] = cscale(buf[i1], (W)1 / (al[0] + k2h));
+        buf[i2] = cscale(buf[i2], (W)1 / (al[1] + k2h));
+        buf[i3] = cscale(buf[i3], (W)1 / (al[2] + k2h));
+      }
     } else {
       const C p1 = buf[i1], p0 = buf[i2], pm = buf[i3];
       // kinetic per component (Parseval): sum 1/2 |k|^2 |phat_l|^2

@@ -452,6 +452,7 @@ OptsDev make_opts(const gpsoc_opts* o) {
   d.sigma = (o->sigma > 0 && o->sigma < 1) ? o->sigma : 0.5;
   d.max_halvings = o->max_halvings > 0 ? o->max_halvings : 40;
   d.no_stop = 0;
+  d.precond = o->precond;
   return d;
 }
 
@@ -865,6 +866,7 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
   if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
   if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
   if (opts->stop < 0 || opts->stop > 3) return fail(GPSOC_EINVAL, "unknown stopping criterion");
+  if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   if (!(opts->tol > 0)) return fail(GPSOC_EINVAL, "tol must be > 0");
   const int levels = opts->cm_levels > 0 ? opts->cm_levels : 1;
   if (levels - 1 > p->max_level) return fail(GPSOC_EINVAL, "too many multigrid levels for this grid");
@@ -905,6 +907,7 @@ gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!opts || iters < 0) return fail(GPSOC_EINVAL, "bad arguments");
+  if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
   OptsDev o = make_opts(opts);
   o.no_stop = 1;
@@ -1194,10 +1197,10 @@ void bucket_free(Bucket* b) {
 
 std::string bucket_key(const ServerReq& r, int stage) {
   char buf[512];
-  std::snprintf(buf, sizeof buf, "%d|%d,%d,%d|%.17g,%.17g,%.17g|%d|%.17g,%.17g,%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d",
+  std::snprintf(buf, sizeof buf, "%d|%d,%d,%d|%.17g,%.17g,%.17g|%d|%.17g,%.17g,%.17g|%.17g|%.17g|%d|%.17g|%.17g|%d|%d|%d",
                 r.grid.dim, r.grid.n[0], r.grid.n[1], r.grid.n[2], r.grid.L[0], r.grid.L[1], r.grid.L[2], r.trap.kind,
                 r.trap.g[0], r.trap.g[1], r.trap.g[2], r.trap.quad, r.trap.quart, r.opts.stop, r.opts.tol,
-                r.opts.res_tol, r.opts.max_iter, stage);
+                r.opts.res_tol, r.opts.max_iter, r.opts.precond, stage);
   return buf;
 }
 
@@ -1353,6 +1356,7 @@ gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const 
   if (trap->kind == GPSOC_TRAP_USER) return fail(GPSOC_EINVAL, "the server takes analytic traps only");
   if (opts->cm_levels > 1) return fail(GPSOC_EINVAL, "the server runs single-level solves (cm_levels = 1)");
   if (!(opts->tol > 0)) return fail(GPSOC_EINVAL, "tol must be > 0");
+  if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   for (int i = 0; i < grid->dim; ++i)
     if (!pow2(grid->n[i]) || grid->n[i] < 8 || grid->n[i] > 1024) return fail(GPSOC_EINVAL, "grid sizes must be powers of two in [8, 1024]");
   if (grid->dim != 2 && grid->dim != 3) return fail(GPSOC_EINVAL, "dim must be 2 or 3");

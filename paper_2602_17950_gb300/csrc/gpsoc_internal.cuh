@@ -115,6 +115,7 @@ struct OptsDev {
   int no_stop;      // gpsoc_iterate: run without stopping tests
   int phase32;      // FP32 phase of a mixed solve: stagnation / iteration cap end the phase, not the solve
   double tol_rel;   // energy stop: |dE| < tol + tol_rel * |E|
+  int precond;      // GPSOC_PRECOND_*
 };
 
 // reduction slots (per solve); partial sums live in part[(s * NSLOT + slot) * pmax + block]

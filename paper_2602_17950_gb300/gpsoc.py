@@ -29,6 +29,10 @@ class GpsocError(RuntimeError):
         self.code = code
 
 
+# GPSOC_PRECOND_*: combined P_C, kinetic P_Delta alone, potential P_V alone, none
+PRECONDS = ("combined", "kinetic", "potential", "none")
+
+
 class Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3)]
 
@@ -46,7 +50,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("tol", C.c_double), ("res_tol", C.c_double),
                 ("max_iter", C.c_int), ("theta_trial", C.c_double), ("sigma", C.c_double),
                 ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int),
-                ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int)]
+                ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int), ("precond", C.c_int)]
 
 
 class Result(C.Structure):
@@ -226,9 +230,10 @@ class Problem:
     @staticmethod
     def opts(precision=GPSOC_FP64, stop=GPSOC_STOP_ENERGY, tol=1e-12, res_tol=0.0, max_iter=100000,
              theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0, fp32_switch=0.0,
-             fp32_min_points=0):
+             fp32_min_points=0, precond="combined"):
+        pk = PRECONDS.index(precond) if isinstance(precond, str) else int(precond)
         return Opts(precision, stop, tol, res_tol, max_iter, theta_trial, sigma, max_halvings, cm_levels,
-                    check_every, fp32_switch, fp32_min_points)
+                    check_every, fp32_switch, fp32_min_points, pk)
 
     # -------------------------------------------------------------- state
     def set_initial(self, psi: np.ndarray, level=0):

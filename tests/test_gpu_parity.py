@@ -364,3 +364,58 @@ def test_fp32_iteration_kernels_run_at_every_tile_shape(n):
             E1, _, m = p.observables()
             assert np.isfinite(E1[0]) and E1[0] < E0
             assert abs(m[0].sum() - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("precond", ["kinetic", "potential", "none"])
+def test_preconditioner_variants_follow_oracle_step_by_step(precond):
+    # P_Delta alone, P_V alone and no preconditioner (Section 3.4): 6 iterations from the
+    # same input follow the oracle's iterations with the same preconditioner
+    n, L = (64, 64), (8.0, 8.0)
+    par = (0.5, 0.5, 100.0, -1.0)
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    m = oracle_model(n, L, par)
+    ref = pcg(m, psi0, Options(tol=1e-300, max_iter=6, precond=precond))
+    assert ref.iters == 6
+    with Problem(n, L, [par]) as p:
+        p.set_initial(psi0[None])
+        res = p.iterate(6, precond=precond)[0]
+        got = p.psi()[0]
+    assert res["iters"] == 6
+    assert rel_max(got, ref.Phi) < 1e-9
+    assert res["energy"] == pytest.approx(ref.energies[-2], rel=1e-12)
+
+
+@pytest.mark.parametrize("precond", ["kinetic", "potential"])
+def test_preconditioner_variants_reach_the_oracle_ground_state(precond):
+    # anisotropic trap: unique minimiser; each preconditioner reaches it (more
+    # iterations than the combined one, as Section 3.4 reports)
+    n, L, par = (32, 32), (6.0, 6.0), (0.4, 0.5, 40.0, -1.0)
+    trap = {"kind": 0, "g": (1.0, 1.15)}
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    m = oracle_model(n, L, par, trap)
+    ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10, precond=precond))
+    with Problem(n, L, [par], trap=trap) as p:
+        p.set_initial(psi0[None])
+        res = p.solve(tol=1e-12, res_tol=2e-10, precond=precond)[0]
+        got = p.psi()[0]
+        p.set_initial(psi0[None])
+        comb = p.solve(tol=1e-12, res_tol=2e-10)[0]
+    _assert_ground_state_parity(m, ref, res, got)
+    assert comb["energy"] == pytest.approx(res["energy"], rel=1e-10)
+    assert comb["total_iters"] < res["total_iters"]
+
+
+@pytest.mark.parametrize("omega", ["0.6", "0.7", "0.8", "0.9"])
+def test_table_cpu_energies_on_the_gpu(omega):
+    # Table table_cpu (Section 4, Example 3): the lowest energies printed to 4 decimals,
+    # reached by CM-PCG 32 -> 64 -> 128 from guess (b) in every component, on the GPU
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table_cpu.json")) as fh:
+        gold = json.load(fh)
+    par = (float(omega), 0.3, 50.0, 0.5)
+    with Problem((128, 128), (12.0, 12.0), [par]) as p:
+        p.set_initial_kind([1, 1, 1], level=2)
+        res = p.solve(tol=1e-10, cm_levels=3, max_iter=200000)[0]
+    assert res["status"] == "OK"
+    assert abs(res["energy"] - gold["lowest_energy"][omega]) <= 0.5e-4
