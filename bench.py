@@ -507,6 +507,54 @@ def case1(args):
     print(json.dumps(out))
 
 
+def traversal(args):
+    """The initial-guess traversal of Section 4, Example 3 (Table table_cpu): for each
+    Omega in {0.6, 0.7, 0.8, 0.9} (gamma = 0.3, beta0 = 50, beta1 = 0.5, harmonic trap,
+    [-12,12]^2), identical components of each guess kind 0..9 (divided by sqrt 3),
+    CM-PCG 32 -> 64 -> 128 to |dE| < 1e-10; all 40 solves advance together in one
+    batched problem; the lowest energy per Omega is kept and compared with the table."""
+    import torch
+    from paper_2602_17950_gb300 import Problem
+    from paper_2602_17950_gb300.build import build
+    build()
+    omegas = (0.6, 0.7, 0.8, 0.9)
+    table = {0.6: 2.2833, 0.7: 2.0437, 0.8: 1.6806, 0.9: 1.0492}   # Table table_cpu, 4 printed digits
+    kinds = list(range(10))
+    n_c, L = (32, 32), (12.0, 12.0)
+    guesses = []
+    for k in kinds:                       # the library's own guess generator, read back
+        with Problem(n_c, L, [(0.0, 0.3, 50.0, 0.5)]) as g:
+            g.set_initial_kind([k, k, k])
+            guesses.append(g.psi()[0])
+    pars, psi0 = [], []
+    for om in omegas:
+        for k in kinds:
+            pars.append((om, 0.3, 50.0, 0.5))
+            psi0.append(guesses[k])
+    out = {"traversal": "Table table_cpu: 4 Omega x 10 guess kinds, CM 32->64->128, |dE|<1e-10, one batch of 40"}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        if name not in args.arms_trav.split(","):
+            continue
+        with Problem((128, 128), L, pars) as p:
+            p.set_initial(np.stack(psi0), level=2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = p.solve(raise_on_error=False, tol=1e-10, cm_levels=3, precision=prec, max_iter=200000)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        lowest = {}
+        for i, r in enumerate(res):
+            om = pars[i][0]
+            if r["status"] == "OK":
+                lowest[om] = min(lowest.get(om, math.inf), r["energy"])
+        out[name] = {"seconds": dt, "solves_per_s": len(pars) / dt,
+                     "converged": sum(r["status"] == "OK" for r in res),
+                     "lowest_energy": {str(om): round(e, 6) for om, e in lowest.items()},
+                     "matches_table_4_digits": {str(om): abs(lowest.get(om, math.inf) - table[om]) <= 0.5e-4
+                                                for om in omegas}}
+    print(json.dumps(out))
+
+
 def case3d(args):
     """The 3D mixed-precision workload: 128^3 on [-8,8]^3, trap (x^2+y^2+4z^2)/2 + 0.1 r^4,
     Omega = 1.2, gamma = 1, beta0 = 500, beta1 = -2, seeded vortex-phase guess, stop
@@ -598,7 +646,12 @@ def main():
     ap.add_argument("--case3d", action="store_true", help="the 3D mixed-precision workload (128^3)")
     ap.add_argument("--n3d", type=int, default=128, help="grid points per axis of --case3d")
     ap.add_argument("--arms3d", default="mixed,fp64", help="arms of --case3d")
+    ap.add_argument("--traversal", action="store_true", help="the initial-guess traversal of Table table_cpu")
+    ap.add_argument("--arms-trav", dest="arms_trav", default="fp64,mixed", help="arms of --traversal")
     args = ap.parse_args()
+    if args.traversal:
+        traversal(args)
+        return
     if args.case1:
         case1(args)
         return
