@@ -419,3 +419,23 @@ def test_table_cpu_energies_on_the_gpu(omega):
         res = p.solve(tol=1e-10, cm_levels=3, max_iter=200000)[0]
     assert res["status"] == "OK"
     assert abs(res["energy"] - gold["lowest_energy"][omega]) <= 0.5e-4
+
+
+@pytest.mark.parametrize("stop,oracle_stop,tol", [(2, "residual", 1e-9), (1, "dphi", 1e-8)])
+def test_stop_criteria_match_oracle(stop, oracle_stop, tol):
+    # stop2 (max_l ||r_l||_inf < tol) and stop1 (max_l ||phi_l^n - phi_l^{n-1}||_inf < tol),
+    # Section 3.4: the GPU stops where the oracle does (up to rounding at the threshold)
+    # and its reported quantity satisfies the criterion
+    n, L, par = (32, 32), (6.0, 6.0), (0.4, 0.5, 40.0, -1.0)
+    trap = {"kind": 0, "g": (1.0, 1.15)}
+    psi0 = si.gaussian_guess(n, L, si.seed_for(1, 0))
+    m = oracle_model(n, L, par, trap)
+    ref = pcg(m, psi0, Options(stop=oracle_stop, tol=tol))
+    with Problem(n, L, [par], trap=trap) as p:
+        p.set_initial(psi0[None])
+        res = p.solve(stop=stop, tol=tol)[0]
+    assert ref.status == "converged" and res["status"] == "OK"
+    assert abs(res["iters"] - ref.iters) <= 2
+    assert res["energy"] == pytest.approx(ref.energy, rel=1e-9)
+    if stop == 2:
+        assert res["res_inf"] < tol
