@@ -122,7 +122,7 @@ __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&sl
 // Working precision W = T: FP64 kernels compute in double, FP32 kernels in float
 // (per-thread partial sums in T, block and grid reductions in FP64).
 template <class T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept) {
+__device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) {
   using C = cx_t<T>;
   using W = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -427,6 +427,24 @@ __global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept
   }
 }
 
+template <class T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_row(ChainArgs<T> A, int R, int ept) {
+  row_pass<T, MODE>(A, R, ept);
+}
+
+// The FP32 inverse passes with fused reductions (the heaviest epilogues) are
+// compiled for three blocks of kThreads per SM (at most 56 registers, a few values
+// spilled): six 192-thread tiles per SM instead of four.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kThreads, 3) k_row_lean(ChainArgs<T> A, int R, int ept) {
+  row_pass<T, MODE>(A, R, ept);
+}
+
+template <class T, int MODE>
+constexpr bool row_lean() {
+  return sizeof(T) == 4 && (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_PRE);
+}
+
 // ============================================================== column passes (y or z axis)
 // Tile: inner indices [i0, i0 + TC) of the axis-`axis` lines at outer index o, all
 // three components.  Shared memory holds every (component, column) line
@@ -723,7 +741,10 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int nb = row_blocks_per_solve<T>(a.g, a.nsolve) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE, a.nsolve);
   const int ept = pick_ept<T>(3 * R * a.g.n[0], a.g.n[0], false);
-  k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
+  if constexpr (row_lean<T, MODE>())
+    k_row_lean<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
+  else
+    k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
 }
 
 template <class T>
@@ -773,6 +794,9 @@ cudaError_t chain_prepare() {
   GPSOC_ATTR((k_row<T, ROW_INV_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_INV_LIN>)) GPSOC_ATTR((k_row<T, ROW_FWD_UPD>))
   GPSOC_ATTR((k_col<T, COL_FWD>)) GPSOC_ATTR((k_col<T, COL_INV>)) GPSOC_ATTR((k_col<T, COL_MID_H>))
   GPSOC_ATTR((k_col<T, COL_MID_PRE>)) GPSOC_ATTR((k_col<T, COL_YMID_H>)) GPSOC_ATTR((k_col<T, COL_YINV_H>))
+  if constexpr (sizeof(T) == 4) {
+    GPSOC_ATTR((k_row_lean<T, ROW_INV_H>)) GPSOC_ATTR((k_row_lean<T, ROW_INV_P>)) GPSOC_ATTR((k_row_lean<T, ROW_INV_PRE>))
+  }
 #undef GPSOC_ATTR
   return e;
 }
