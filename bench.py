@@ -127,6 +127,12 @@ KERNEL_WORK = {
 }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu
+# on the kernel inside this workload: (kernel, grid points per axis, 1 = FP32 / 0 = FP64).
+# At 128^2 the arrays stay in L2 (0 bytes written back during the launch).
+NCU_DRAM_BYTES = {("coly_ymid_h", 128, 0): 869888.0}
+
+
 def kernel_flops(name: str, n) -> float:
     """Algorithmic flops of one launch of a 2D pass on one solve (3 components):
     the 1-D FFTs it performs, 5 n log2 n each; pointwise work is not counted."""
@@ -313,6 +319,7 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "FP64 FMA-chain probe gpsoc_probe_peaks, this run (of measured)",
                 "algorithmic_flops_per_launch": fl}
     roof.update({"ms_per_launch": dom_ms, "share_of_solve": shares[(dom_name, dom_n, dom_pr)] / total_share})
+    roof["traffic"] = NCU_DRAM_BYTES.get((dom_name, dom_n, dom_pr))
     ms_per_step = max_total_ms / args.steps
     out = {
         "metric": METRIC, "value": whole_job_rate(world, args.steps, max_total_ms), "unit": "solves/s",
