@@ -1,7 +1,7 @@
 """GPU parity: every step of the hot path through the C ABI against the FP64 oracle.
 
 Tolerances (FP64 path): operator outputs within 1e-11 of the oracle's max
-magnitude (radix-2 FFT rounding grows like eps * log2(N) per transform, a few
+magnitude (FFT rounding grows like eps * log2(N) per transform, a few
 transforms per operator); scalar reductions (E, mu, alpha, masses, a_n, b_n)
 within 1e-12 relative; converged ground states: E and mu within 1e-10 relative,
 densities and component masses within 1e-8 in max norm (BASELINE targets)."""
