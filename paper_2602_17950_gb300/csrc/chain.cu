@@ -596,9 +596,15 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
       // P_Delta (Eq. PreCondKin); the potential-only and no-preconditioner variants keep
       // the coefficients (the transform pair is then the identity up to rounding)
       if (use_pd) {
-        buf[i1] = cscale(buf[i1], (W)1 / (al[0] + k2h));
-        buf[i2] = cscale(buf[i2], (W)1 / (al[1] + k2h));
-        buf[i3] = cscale(buf[i3], (W)1 / (al[2] + k2h));
+        // the three reciprocals from one division (an FP64 division is a long
+        // instruction sequence): 1/d0 = d1 d2 / (d0 d1 d2), and so on
+        const W d0 = al[0] + k2h, d1 = al[1] + k2h, d2 = al[2] + k2h;
+        const W d01 = d0 * d1;
+        const W inv = (W)1 / (d01 * d2);
+        const W r01 = d2 * inv;
+        buf[i1] = cscale(buf[i1], d1 * r01);
+        buf[i2] = cscale(buf[i2], d0 * r01);
+        buf[i3] = cscale(buf[i3], d01 * inv);
       }
     } else {
       const C p1 = buf[i1], p0 = buf[i2], pm = buf[i3];
