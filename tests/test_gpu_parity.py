@@ -439,3 +439,48 @@ def test_stop_criteria_match_oracle(stop, oracle_stop, tol):
     assert res["energy"] == pytest.approx(ref.energy, rel=1e-9)
     if stop == 2:
         assert res["res_inf"] < tol
+
+
+_TRAP3 = {"kind": 1, "g": (1.0, 1.1, 2.0), "quad": 0.0, "quart": 0.02}
+
+
+def test_3d_cascadic_multigrid_matches_oracle():
+    # Algorithm 3 in 3D: 8^3 -> 16^3 by spectral zero padding, anisotropic harmonic-plus-quartic trap
+    L, par = (5.0, 5.0, 5.0), (0.4, 0.5, 30.0, -1.0)
+    models = [oracle_model((k, k, k), L, par, _TRAP3) for k in (8, 16)]
+    psi0 = si.gaussian_guess((8, 8, 8), L, 93)
+    ref, _ = cm_pcg(models, psi0, Options(tol=1e-12, res_tol=1e-9))
+    with Problem((16, 16, 16), L, [par], trap=_TRAP3) as p:
+        p.set_initial(psi0[None], level=1)
+        res = p.solve(tol=1e-12, res_tol=1e-9, cm_levels=2)[0]
+        got = p.psi()[0]
+    assert res["levels"] == 2 and res["total_iters"] > res["iters"]
+    _assert_ground_state_parity(models[-1], ref, res, got)
+
+
+def test_3d_kinetic_preconditioner_follows_oracle_step_by_step():
+    # the 3D preconditioner chain (y forward, z kinetic division, y inverse) with P_Delta alone
+    n, L, par = (16, 16, 16), (5.0, 5.0, 5.0), (0.4, 0.5, 30.0, -1.0)
+    psi0 = si.gaussian_guess(n, L, 94)
+    m = oracle_model(n, L, par, _TRAP3)
+    ref = pcg(m, psi0, Options(tol=1e-300, max_iter=6, precond="kinetic"))
+    with Problem(n, L, [par], trap=_TRAP3) as p:
+        p.set_initial(psi0[None])
+        res = p.iterate(6, precond="kinetic")[0]
+        got = p.psi()[0]
+    assert res["iters"] == 6
+    assert rel_max(got, ref.Phi) < 1e-9
+
+
+def test_3d_mixed_precision_ground_state_matches_oracle():
+    # FP32 phase forced on a small 3D grid, then FP64 polish: the oracle's FP64 ground state
+    n, L, par = (16, 16, 16), (5.0, 5.0, 5.0), (0.4, 0.5, 30.0, -1.0)
+    psi0 = si.gaussian_guess(n, L, 94)
+    m = oracle_model(n, L, par, _TRAP3)
+    ref = pcg(m, psi0, Options(tol=1e-12, res_tol=2e-10))
+    with Problem(n, L, [par], trap=_TRAP3) as p:
+        p.set_initial(psi0[None])
+        res = p.solve(tol=1e-12, res_tol=2e-10, precision=1, fp32_min_points=-1)[0]
+        got = p.psi()[0]
+    assert res["fp32_iters"] > 0 and res["fp64_iters"] > 0
+    _assert_ground_state_parity(m, ref, res, got)
