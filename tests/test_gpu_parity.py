@@ -484,3 +484,29 @@ def test_3d_mixed_precision_ground_state_matches_oracle():
         got = p.psi()[0]
     assert res["fp32_iters"] > 0 and res["fp64_iters"] > 0
     _assert_ground_state_parity(m, ref, res, got)
+
+
+def test_user_potential_ground_state_matches_oracle():
+    # a user-supplied potential array on top of the harmonic trap, through every kernel that reads V
+    n, L = (32, 32), (6.0, 6.0)
+    X, Y = si.mesh(n, L)
+    V = 0.3 * np.cos(X) * np.sin(0.5 * Y) + 0.1 * X
+    trap = {"kind": 2, "g": (1.0, 1.15), "user_V": V}
+    psi0 = si.gaussian_guess(n, L, 95)
+    _assert_ground_state_parity(*_solve_pair(n, L, (0.3, 0.5, 40.0, -1.0), psi0, res_tol=2e-10, trap=trap))
+
+
+def test_batched_parameters_match_individual_oracle_solves():
+    # one batch, three parameter sets: each solve against its own oracle solve
+    n, L = (32, 32), (6.0, 6.0)
+    trap = {"kind": 0, "g": (1.0, 1.15)}
+    pars = [(0.2, 0.3, 20.0, -1.0), (0.5, 1.0, 60.0, 2.0), (0.0, 0.0, 10.0, 0.0)]
+    psi0 = [si.gaussian_guess(n, L, 96 + k) for k in range(3)]
+    with Problem(n, L, pars, trap=trap) as p:
+        p.set_initial(np.stack(psi0))
+        res = p.solve(tol=1e-12, res_tol=2e-10)
+        got = p.psi()
+    for k in range(3):
+        m = oracle_model(n, L, pars[k], trap)
+        ref = pcg(m, psi0[k], Options(tol=1e-12, res_tol=2e-10))
+        _assert_ground_state_parity(m, ref, res[k], got[k])
