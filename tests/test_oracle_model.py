@@ -255,3 +255,77 @@ def test_energy_change_expansion_matches_direct_difference():
     for t in (1.3, 0.4, 0.05, 1e-3):
         direct = m.energy(math.cos(t) * Phi + math.sin(t) * Ph) - E0
         assert m.energy_change(Phi, Ph, t) == pytest.approx(direct, rel=1e-9, abs=1e-12)
+
+
+# ---------------------------------------------------------------- preconditioners pinned in closed form
+def _plane_waves(m, waves, amps=(1.0, 1.0, 1.0)):
+    """Component l = amps[l] exp(i k_l . x) with k_l on the grid's wavenumber lattice
+    (waves[l] = integer multiples of pi/L_i per axis)."""
+    g = m.grid
+    out = []
+    for c in range(3):
+        ph = sum(math.pi * waves[c][i] / g.L[i] * g.X[i] for i in range(g.d))
+        out.append(amps[c] * np.exp(1j * ph) * np.ones(g.shape))
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("n,L", [((16, 16), (4.0, 4.0)), ((8, 16, 8), (3.0, 4.0, 2.5))])
+def test_kinetic_preconditioner_divides_plane_waves_by_alpha_plus_half_k2(n, L):
+    # P_Delta (Eq. PreCondKin) is the Fourier multiplier 1/(alpha_l + |k|^2/2): a plane wave
+    # exp(i k.x) in component l comes back scaled by exactly that factor
+    m = _model(n, L)
+    d = len(n)
+    waves = [(3, -2, 1)[:d], (0, 5, -3)[:d], (-4, 1, 2)[:d]]
+    W = _plane_waves(m, waves, (1.0, 0.5 - 0.3j, 2.0))
+    alpha = [0.7, 1.3, 2.1]
+    out = m.precond_Delta(W, alpha)
+    for c in range(3):
+        k2 = sum((math.pi * waves[c][i] / L[i]) ** 2 for i in range(d))
+        np.testing.assert_allclose(out[c], W[c] / (alpha[c] + 0.5 * k2), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(m.precond_kin(W, W, alpha), out, rtol=1e-14, atol=1e-16)
+
+
+def test_potential_preconditioner_is_pointwise_inverse_of_alpha_plus_V_plus_c0_rho():
+    # P_V (Eq. PreCondPot) multiplies component l by 1/(alpha_l + V + c0 rho); the square-root
+    # factor of P_C by 1/sqrt(alpha_l + V + c0 rho); V = (gx^2 x^2 + gy^2 y^2)/2 typed here
+    c0 = 7.5
+    m = _model((16, 16), (4.0, 4.0), trap=Trap(g=(1.0, 1.7)), c0=c0)
+    X, Y = m.grid.X
+    V = 0.5 * (X * X + (1.7 * Y) ** 2)
+    Phi = _smooth(m, 31)
+    rho = sum(np.abs(Phi[c]) ** 2 for c in range(3))
+    r = si.random_state(m.grid.n, 32)
+    alpha = [0.4, 0.9, 3.2]
+    s = m.precond_V_sqrt(Phi, alpha)
+    pot = m.precond_pot(r, Phi, alpha)
+    for c in range(3):
+        den = alpha[c] + V + c0 * rho
+        np.testing.assert_allclose(s[c], 1.0 / np.sqrt(den), rtol=1e-14)
+        np.testing.assert_allclose(pot[c], r[c] / den, rtol=1e-13)
+
+
+@pytest.mark.parametrize("n,L", [((16, 16), (4.0, 4.0)), ((8, 8, 16), (3.0, 3.0, 4.0))])
+def test_combined_preconditioner_and_alpha_closed_form_on_uniform_density(n, L):
+    # V = 0 and plane-wave components a_l exp(i k_l.x): rho = sum |a_l|^2 is constant, so
+    #   alpha_l = |a_l|^2 |D| (|k_l|^2/2 + c0 rho)       (Eq. PreCnstAlpha, |D| = prod 2 L_i)
+    #   P_C exp(i q.x) e_l = exp(i q.x) e_l / ((alpha_l + c0 rho)(alpha_l + |q|^2/2))   (Eq. PreCondMix)
+    # (each half of P_V^{1/2} contributes (alpha_l + c0 rho)^{-1/2}; P_Delta the kinetic factor)
+    c0 = 3.0
+    d = len(n)
+    m = _model(n, L, trap=Trap(g=(0.0, 0.0, 0.0)), c0=c0, c1=-1.0, Omega=0.2, gamma=0.4)
+    amps = (0.6, 0.3 + 0.2j, 0.25)
+    kw = [(1, 2, 1)[:d], (-2, 0, 1)[:d], (0, -1, -2)[:d]]
+    Phi = _plane_waves(m, kw, amps)
+    rho = sum(abs(a) ** 2 for a in amps)
+    vol = float(np.prod([2 * Li for Li in L]))
+    alpha = m.alpha(Phi)
+    for c in range(3):
+        k2 = sum((math.pi * kw[c][i] / L[i]) ** 2 for i in range(d))
+        assert alpha[c] == pytest.approx(abs(amps[c]) ** 2 * vol * (0.5 * k2 + c0 * rho), rel=1e-12)
+    qw = [(3, -1, 2)[:d], (0, 4, -1)[:d], (-2, -3, 1)[:d]]
+    r = _plane_waves(m, qw, (1.0, -0.7j, 0.4))
+    z = m.precond_C(r, Phi, alpha)
+    for c in range(3):
+        q2 = sum((math.pi * qw[c][i] / L[i]) ** 2 for i in range(d))
+        fac = 1.0 / ((alpha[c] + c0 * rho) * (alpha[c] + 0.5 * q2))
+        np.testing.assert_allclose(z[c], fac * r[c], rtol=1e-12, atol=1e-15)
