@@ -41,8 +41,13 @@ L_BOX = (16.0, 16.0)
 LEVELS = 3
 PAR = (0.9, 1.0, 1000.0, -5.0)
 TOL = 1e-12
+RES_TOL = 1e-8
 WORKLOAD = ("2D CM-PCG 128->256->512, 512x512 on [-16,16]^2, harmonic trap, Omega=0.9, gamma=1, "
-            "beta0=1000, beta1=-5, seeded vortex-phase guess, stop |dE|<1e-12")
+            "beta0=1000, beta1=-5, seeded vortex-phase guess, stop |dE|<1e-12 and max|r|<1e-8 on every level")
+# Per-level iteration counts (128^2, 256^2, 512^2) of one plain FP64 solve of this workload, as the
+# FP64 arm of the main run reports them in `fp64_plain.level_iters` (the GPU path follows the
+# oracle's iterations step by step); the reference arm scales its timed oracle sample by them.
+REF_LEVEL_ITERS = (38561, 29677, 17)
 L2_BYTES = 256 << 20
 
 
@@ -149,6 +154,48 @@ def kernel_bytes(name: str, n, elem: int) -> float:
 
 
 # ------------------------------------------------------------------ oracle (CPU) sample
+def cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, or lscpu on Arm)."""
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_worker(iters_per_level):
+    import os as _os
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        _os.environ[v] = "1"
+    return oracle_sample(iters_per_level)[0]
+
+
+def oracle_baseline(iters_per_level):
+    """The oracle timed on one host core and on all of them: the single-core solve time
+    (per-level sample x iteration counts) and the throughput of independent solves, one
+    per core, all cores busy at once (spawned worker processes)."""
+    import multiprocessing as mp
+    t1, desc = oracle_sample(iters_per_level)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        times = pool.map(_oracle_worker, [tuple(iters_per_level)] * cores)
+    rate_all = sum(1.0 / t for t in times)
+    return {"value": rate_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "single_core_value": 1.0 / t1, "cpu_model": cpu_model(), "nproc": cores,
+            "sample": desc + f"; all {cores} cores: one independent oracle sample per core at once, "
+                             "throughput = sum of their rates (extrapolated solves, not whole solves)"}
+
+
 def oracle_sample(iters_per_level, budget_s: float = 20.0):
     """Time the FP64 CPU oracle's PCG iterations on each level of the workload and
     scale by the iteration counts of a full solve.  Returns (seconds per solve,
@@ -232,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
     d_psi0 = torch.from_numpy(psi0[None].copy()).to(dev)
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
     prob = Problem(N_FINE, L_BOX, [PAR])
-    opts = dict(precision=prec, tol=TOL, cm_levels=LEVELS, check_every=64)
+    opts = dict(precision=prec, tol=TOL, res_tol=RES_TOL, cm_levels=LEVELS, check_every=64)
     dist = world > 1
     if dist:
         import torch.distributed as tdist
@@ -256,16 +303,17 @@ def run_ours(args, rank, world, local_rank):
         lat64, res64 = timed_solves(prob, dict(opts, precision=0), d_psi0, flush, stream, 1, args.fp64_steps, torch)
         fp64 = {"value": world * 1000.0 / statistics.mean(lat64), "unit": "solves/s",
                 "ms_per_solve": statistics.mean(lat64), "p50_ms": float(np.percentile(lat64, 50)),
-                "p99_ms": float(np.percentile(lat64, 99)), "status_ok": all(r["status"] == "OK" for r in res64),
-                "energy": res64[-1]["energy"], "iters_total": res64[-1]["total_iters"],
-                "level_iters": res64[-1]["level_iters"]}
+                "p99_ms": float(np.percentile(lat64, 99)), "samples": len(lat64),
+                "status_ok": all(r["status"] == "OK" for r in res64),
+                "energy": res64[-1]["energy"], "mu": res64[-1]["mu"], "res_inf": res64[-1]["res_inf"],
+                "iters_total": res64[-1]["total_iters"], "level_iters": res64[-1]["level_iters"]}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     h_in = torch.empty(psi0[None].shape, dtype=torch.complex128, pin_memory=True)
     h_in.numpy()[...] = psi0[None]
     h_out = torch.empty((1, 3) + tuple(N_FINE[::-1]), dtype=torch.complex128, pin_memory=True)
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 3)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -335,9 +383,14 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "kernels_us_per_iteration": {f"{n}_{'fp32' if pr else 'fp64'}": {k: round(v * 1e3, 2) for k, v in pl_ms}
                                      for (n, pr), (_, pl_ms) in prof.items()},
-        "solve": {"status_ok": ok, "energy": last["energy"], "mu": last["mu"], "iters_total": last["total_iters"],
-                  "level_iters": last["level_iters"], "level_fp32_iters": fp32_lv, "fp32_iters": last["fp32_iters"],
-                  "fp64_iters": last["fp64_iters"], "beta_resets": last["beta_resets"]},
+        "solve": {"status_ok": ok, "energy": last["energy"], "mu": last["mu"], "res_inf": last["res_inf"],
+                  "iters_total": last["total_iters"], "level_iters": last["level_iters"],
+                  "level_fp32_iters": fp32_lv, "level_res_fp32": last.get("level_res_fp32"),
+                  "fp32_iters": last["fp32_iters"], "fp64_iters": last["fp64_iters"],
+                  "beta_resets": last["beta_resets"],
+                  "energy_rel_diff_vs_fp64_plain": (abs(last["energy"] - fp64["energy"]) / abs(fp64["energy"])
+                                                    if fp64 else None),
+                  "stop": f"|dE| < {TOL:g} and max|r| < {RES_TOL:g} on every level (both arms)"},
         "e2e": {"value": world / statistics.mean(e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h_in.numpy().nbytes), "d2h_bytes_per_step": int(h_out.numpy().nbytes)},
         "gpu_launches": launches_timed,
@@ -360,19 +413,22 @@ def batch_case(args):
     B = args.batch
     pars = [(q.Omega, q.gamma, q.beta0, q.beta1) for q in si.batch_params(si.seed_for(3, 0), B)]
     psi = np.stack([si.gaussian_guess(n, L, si.seed_for(3, k), vortex=bool(k % 2)) for k in range(B)])
-    out = {"workload": f"{B} solves of 256x256 on [-12,12]^2, random parameters, stop |dE|<1e-12",
+    out = {"workload": f"{B} solves of 256x256 on [-12,12]^2, random parameters, stop |dE|<1e-12 and "
+                       f"max|r|<{args.serve_res_tol:g}",
            "max_iter": args.max_iter}
     for name, prec in (("fp64", 0), ("mixed", 1)):
         with Problem(n, L, pars) as p:
             p.set_initial(psi)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = p.solve(tol=TOL, precision=prec, max_iter=args.max_iter, check_every=64)
+            res = p.solve(raise_on_error=False, tol=TOL, res_tol=args.serve_res_tol, precision=prec,
+                          max_iter=args.max_iter, check_every=64)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
         ok = sum(r["status"] == "OK" for r in res)
         its = [r["total_iters"] for r in res]
-        out[name] = {"seconds": dt, "solves_per_s": B / dt, "converged": ok,
+        out[name] = {"seconds": dt, "solves_per_s": B / dt, "converged": ok, "converged_solves_per_s": ok / dt,
+                     "status_counts": {st: sum(r["status"] == st for r in res) for st in sorted({r["status"] for r in res})},
                      "iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)),
                      "fp32_iters_mean": float(np.mean([r["fp32_iters"] for r in res])),
                      "energies": [r["energy"] for r in res]}
@@ -387,23 +443,26 @@ def batch_case(args):
     print(json.dumps(out))
 
 
-def serve_case(args):
-    """The served trace: `requests` ground-state requests with Poisson arrivals,
-    grids drawn from {64^2, 128^2, 256^2, 512^2, 64^3, 128^3}, parameters drawn as
-    in the batched sweep, harmonic traps (3D: gamma_z = 2), stop |dE| < serve_tol.
-    Three arms on the same trace: the continuous-batching server in mixed
-    precision and in FP64, and plain single-solve FP64 PCG serving the requests
-    one at a time in arrival order.  Reports solves/s over the makespan and the
-    p50/p99 of arrival-to-result latency (wall clock)."""
+def serve_trace_run(requests, rate, tol, res_tol, arms, max_iter, hbm_budget, slots, seed=None):
+    """The served trace: `requests` ground-state requests with Poisson arrivals at
+    `rate` per second, grids drawn from {64^2, 128^2, 256^2, 512^2, 64^3, 128^3},
+    parameters drawn as in the batched sweep, harmonic traps (3D: gamma_z = 2),
+    stop |dE| < tol and max|r| < res_tol.  Arms on the same trace: the
+    continuous-batching server in mixed precision ("served_mixed") and in FP64
+    ("served_fp64"), and plain single-solve FP64 PCG serving the requests one at a
+    time in arrival order ("plain_fp64").  Reports solves/s over the makespan, the
+    p50/p99 of arrival-to-result latency (wall clock), and, against plain FP64, the
+    number of results in the same minimum (energies within 1e-10 relative) and the
+    speed-up counted over those results only."""
     import torch
     from paper_2602_17950_gb300 import Problem, Server
     from paper_2602_17950_gb300.build import build
     build()
-    trace = si.serve_trace(si.seed_for(5, 0), args.requests, args.arrival_rate)
+    trace = si.serve_trace(si.seed_for(5, 0) if seed is None else seed, requests, rate)
     R = len(trace)
     guesses = [si.gaussian_guess(q["n"], q["L"], q["guess_seed"], vortex=q["vortex"]) for q in trace]
     traps = [{"kind": 0, "g": (1.0, 1.0, 2.0) if len(q["n"]) == 3 else (1.0, 1.0)} for q in trace]
-    opts = dict(tol=args.serve_tol, max_iter=args.max_iter)
+    opts = dict(tol=tol, res_tol=res_tol, max_iter=max_iter)
 
     def par(q):
         p = q["params"]
@@ -417,7 +476,7 @@ def serve_case(args):
 
     def served(precision):
         done, res = {}, [None] * R
-        with Server(hbm_budget_bytes=args.hbm_budget, slots_per_bucket=args.slots, precision=precision,
+        with Server(hbm_budget_bytes=hbm_budget, slots_per_bucket=slots, precision=precision,
                     iters_per_step=32) as sv:
             t0 = time.perf_counter()
             nxt, tickets = 0, {}
@@ -438,43 +497,58 @@ def serve_case(args):
                     time.sleep(max(0.0, trace[nxt]["arrival"] - (time.perf_counter() - t0)))
             span = max(done.values())
         lat = [done[k] - trace[k]["arrival"] for k in range(R)]
-        return summarise(lat, span, res), res
+        return summarise(lat, span, res), res, None
 
     def plain():
-        res, lat = [None] * R, [0.0] * R
+        res, lat, service = [None] * R, [0.0] * R, [0.0] * R
         t0 = time.perf_counter()
         for k, q in enumerate(trace):
             wait = q["arrival"] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
+            ts = time.perf_counter()
             with Problem(q["n"], q["L"], [par(q)], trap=traps[k]) as p:
                 p.set_initial(guesses[k][None])
                 res[k] = p.solve(raise_on_error=False, precision=0, **opts)[0]
             torch.cuda.synchronize()
+            service[k] = time.perf_counter() - ts
             lat[k] = time.perf_counter() - t0 - q["arrival"]
         span = time.perf_counter() - t0
-        return summarise(lat, span, res), res
+        return summarise(lat, span, res), res, service
 
-    out = {"serve_case": f"{R} requests, Poisson {args.arrival_rate}/s, grids 64^2..512^2, 64^3, 128^3, "
-                         f"stop |dE|<{args.serve_tol:g}, max_iter {args.max_iter}",
+    out = {"trace": f"{R} requests, Poisson {rate}/s, grids 64^2..512^2, 64^3, 128^3, "
+                    f"stop |dE|<{tol:g} and max|r|<{res_tol:g}, max_iter {max_iter}",
            "grid_mix": {f"{'x'.join(map(str, n))}": sum(q["n"] == n for q in trace) for n, _ in si.SERVE_GRIDS},
-           "hbm_budget_gb": args.hbm_budget / 1e9, "slots_per_bucket": args.slots}
-    arms = {}
-    for name, fn in (("served_mixed", lambda: served(1)), ("served_fp64", lambda: served(0)), ("plain_fp64", plain)):
-        if name in args.arms.split(","):
-            out[name], arms[name] = fn()
-    if "plain_fp64" in arms:
-        ref = arms["plain_fp64"]
-        for name, rs in arms.items():
-            if name != "plain_fp64":
-                d = [abs(a["energy"] - b["energy"]) / abs(b["energy"]) for a, b in zip(rs, ref)
-                     if a["status"] == "OK" and b["status"] == "OK"]
-                out[name]["energy_rel_diff_vs_plain_max"] = float(max(d)) if d else None
-                out[name]["same_minimum_as_plain_1e-8"] = int(sum(x < 1e-8 for x in d))
-                out[name]["lower_energy_than_plain"] = int(sum(a["energy"] < b["energy"] - 1e-8 * abs(b["energy"])
-                                                               for a, b in zip(rs, ref)))
-                out[name]["speedup_vs_plain"] = out[name]["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
-    print(json.dumps(out))
+           "hbm_budget_gb": hbm_budget / 1e9, "slots_per_bucket": slots}
+    runs = {}
+    for name, fn in (("plain_fp64", plain), ("served_mixed", lambda: served(1)), ("served_fp64", lambda: served(0))):
+        if name in arms:
+            out[name], rs, service = fn()
+            runs[name] = (rs, service)
+    if "plain_fp64" in runs:
+        ref, service = runs["plain_fp64"]
+        for name, (rs, _) in runs.items():
+            if name == "plain_fp64":
+                continue
+            both = [k for k in range(R) if rs[k]["status"] == "OK" and ref[k]["status"] == "OK"]
+            d = {k: abs(rs[k]["energy"] - ref[k]["energy"]) / abs(ref[k]["energy"]) for k in both}
+            same = [k for k in both if d[k] <= 1e-10]
+            o = out[name]
+            o["energy_rel_diff_vs_plain_max"] = float(max(d.values())) if d else None
+            o["same_minimum_as_plain_1e-10"] = len(same)
+            o["same_minimum_fraction"] = len(same) / R
+            o["lower_energy_than_plain"] = int(sum(rs[k]["energy"] < ref[k]["energy"] * (1 + 1e-10 * np.sign(ref[k]["energy"]))
+                                                   for k in both if k not in same))
+            o["speedup_vs_plain"] = o["solves_per_s"] / out["plain_fp64"]["solves_per_s"]
+            # over the same-minimum results only: their plain service time against the served makespan
+            o["speedup_vs_plain_same_minimum"] = (sum(service[k] for k in same) / o["makespan_s"]) if same else None
+    return out
+
+
+def serve_case(args):
+    """The served trace as its own command (see serve_trace_run)."""
+    print(json.dumps(serve_trace_run(args.requests, args.arrival_rate, args.serve_tol, args.serve_res_tol,
+                                     args.arms.split(","), args.max_iter, args.hbm_budget, args.slots)))
 
 
 def case1(args):
@@ -634,21 +708,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
-    ap.add_argument("--fp64-steps", type=int, default=2, help="timed solves of the plain FP64 comparison")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="timed solves of the plain FP64 comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="N",
                     help="only time the kernels of PCG iterations on N x N grids (per-kernel CUDA events)")
     ap.add_argument("--batch", type=int, default=1, help="solves per problem in --kernel-case / --batch-case")
     ap.add_argument("--batch-case", action="store_true", help="the batched random-parameter sweep at 256^2")
-    ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of --batch-case / --serve-case")
+    ap.add_argument("--max-iter", type=int, default=50000, help="iteration cap of the batched and served cases")
     ap.add_argument("--serve-case", action="store_true", help="the served trace (Poisson arrivals, mixed grids)")
     ap.add_argument("--requests", type=int, default=32, help="requests of --serve-case")
-    ap.add_argument("--arrival-rate", type=float, default=4.0, help="Poisson arrival rate of --serve-case (1/s)")
-    ap.add_argument("--serve-tol", type=float, default=1e-10, help="energy stopping tolerance of --serve-case")
+    ap.add_argument("--arrival-rate", type=float, default=4.0, help="Poisson arrival rate of the served trace (1/s)")
+    ap.add_argument("--serve-tol", type=float, default=1e-12, help="energy stopping tolerance of the served trace")
+    ap.add_argument("--serve-res-tol", type=float, default=1e-8, help="residual tolerance of the served trace")
+    ap.add_argument("--serve-sample", type=int, default=128,
+                    help="requests of the served-trace sample in the default run (0 = none)")
     ap.add_argument("--hbm-budget", type=float, default=120e9, help="device bytes the server may use")
     ap.add_argument("--slots", type=int, default=16, help="solves per server bucket")
     ap.add_argument("--arms", default="served_mixed,served_fp64,plain_fp64", help="arms of --serve-case")
+    ap.add_argument("--sample-arms", default="plain_fp64,served_mixed", help="arms of the default run's served sample")
     ap.add_argument("--case1", action="store_true", help="the small 64^2 plain-PCG workload vs the oracle")
     ap.add_argument("--case3d", action="store_true", help="the 3D mixed-precision workload (128^3)")
     ap.add_argument("--n3d", type=int, default=128, help="grid points per axis of --case3d")
@@ -688,35 +766,27 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # iteration counts of one solve from the GPU path (untimed), then the oracle's per-level cost
-        iters_lv = None
-        try:
-            import torch
-            if torch.cuda.is_available():
-                from paper_2602_17950_gb300 import Problem
-                from paper_2602_17950_gb300.build import build
-                build()
-                with Problem(N_FINE, L_BOX, [PAR]) as p:
-                    p.set_initial(initial_guess(0)[None], level=LEVELS - 1)
-                    r = p.solve(tol=TOL, cm_levels=LEVELS)[0]
-                iters_lv = per_level_iters(r, LEVELS)
-        except Exception:
-            iters_lv = None
-        if iters_lv is None:
-            iters_lv = [1000.0, 300.0, 300.0]
-        times = []
-        desc = ""
-        oracle_sample(iters_lv)                 # one untimed warm-up sample (pages in numpy)
+        # the FP64 CPU oracle on this machine's host cores: per-level iteration times of the
+        # workload, scaled by the per-level iteration counts of one solve (REF_LEVEL_ITERS);
+        # one sample per step on all cores at once (independent solves, one per core)
+        times, cores, desc, single = [], 1, "", []
+        oracle_sample(REF_LEVEL_ITERS)          # one untimed warm-up sample (pages in numpy)
         for _ in range(args.steps):
-            t, desc = oracle_sample(iters_lv)
-            times.append(t)
+            b = oracle_baseline(REF_LEVEL_ITERS)
+            times.append(1.0 / b["value"])
+            single.append(b["single_core_value"])
+            cores, desc = b["cores"], b["sample"]
         v = 1.0 / statistics.mean(times)
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(times),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": {"workload": WORKLOAD, "global_batch": 1, "grid": "512x512",
                                                "levels": [128, 256, 512], "precision": "fp64"},
-               "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+               "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "single_core_value": statistics.mean(single), "cpu_model": cpu_model(),
+                                "nproc": os.cpu_count(),
+                                "sample": desc + f"; per-level iteration counts {list(REF_LEVEL_ITERS)} of one "
+                                                 "plain FP64 solve (extrapolated, not a whole solve)"},
                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
@@ -729,9 +799,18 @@ def main():
     if rank != 0 or got is None:
         return
     out, last = got
+    if args.serve_sample > 0 and world == 1:
+        # the spec comparison on the device: a bounded sample of the served trace,
+        # batched mixed-precision server against plain single-solve FP64, same stopping rule
+        with ClockSampler(local_rank) as clk:
+            out["served_trace"] = serve_trace_run(args.serve_sample, args.arrival_rate, args.serve_tol,
+                                                  args.serve_res_tol, args.sample_arms.split(","), args.max_iter,
+                                                  args.hbm_budget, args.slots)
+        out["served_trace"]["clocks"] = clk.summary()
     if not args.no_cpu and world == 1:
-        t, desc = oracle_sample(per_level_iters(last, LEVELS))
-        out["cpu_baseline"] = {"value": 1.0 / t, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+        fp = out.get("fp64_plain") or {}
+        its = fp.get("level_iters") or per_level_iters(last, LEVELS)
+        out["cpu_baseline"] = oracle_baseline(its)
     print(json.dumps(out))
 
 

@@ -46,7 +46,8 @@ typedef enum {
   GPSOC_ETIMEOUT = 6,    /* a bounded host wait ran out */
   GPSOC_ESTATE = 7,      /* call made in the wrong state (e.g. solve before set_initial) */
   GPSOC_EBUDGET = 8,     /* the request does not fit the memory budget */
-  GPSOC_ESTAGNATED = 9   /* Algorithm 2 found no energy decrease (converged to rounding) */
+  GPSOC_ESTAGNATED = 9,  /* Algorithm 2 found no energy decrease (converged to rounding) */
+  GPSOC_ECANCELED = 10   /* a served request was withdrawn by gpsoc_server_cancel */
 } gpsoc_status;
 
 enum { GPSOC_TRAP_HARMONIC = 0, GPSOC_TRAP_HARMONIC_QUARTIC = 1, GPSOC_TRAP_USER = 2 };
@@ -105,7 +106,15 @@ typedef struct {
  *                grid points fall below this runs in FP64 alone, since FP32
  *                arrays save little on work that is bound by launch latency;
  *                0 selects 65536, a negative value gives every level an FP32 phase.
- *   precond      GPSOC_PRECOND_* (0 = the combined preconditioner). */
+ *   precond      GPSOC_PRECOND_* (0 = the combined preconditioner).
+ *   fp32_res_switch  GPSOC_MIXED only: the FP32 phase of a level also ends once
+ *                max_l ||r_l||_inf < fp32_res_switch, and takes no step when the
+ *                level starts below it (0 = no residual rule).
+ *   fp32_carry   GPSOC_MIXED only: 0 restarts the FP64 phase of a level with
+ *                beta = 0; 1 continues it from the FP32 phase's last direction
+ *                (beta, r_prev, P_prev carried over; measured slower on the 512^2
+ *                workload, so off by default).  A solve that took no FP32 step on a
+ *                level keeps its FP64 state unchanged. */
 typedef struct {
   int precision;
   int stop;
@@ -119,13 +128,16 @@ typedef struct {
   double fp32_switch;
   int fp32_min_points;
   int precond;
+  double fp32_res_switch;
+  int fp32_carry;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;
  * res_inf = max_l ||r_l||_inf of that iterate; dE_last = energy change of the
  * last accepted step; level_iters[k] = iterations on multigrid level k
  * (k = 0 the coarsest, at most 8 levels), level_fp32_iters[k] = those of them
- * taken in FP32 arrays (GPSOC_MIXED). */
+ * taken in FP32 arrays (GPSOC_MIXED), level_res_fp32[k] = max_l ||r_l||_inf where
+ * level k's FP32 phase ended (0 if it had none). */
 typedef struct {
   int status;            /* gpsoc_status of this solve */
   int iters;             /* iterations on the finest level */
@@ -135,6 +147,7 @@ typedef struct {
   double energy, mu, mass[3], res_inf, dE_last;
   int level_iters[8];
   int level_fp32_iters[8];
+  double level_res_fp32[8];
 } gpsoc_result;
 
 typedef struct gpsoc_problem gpsoc_problem;
@@ -178,7 +191,11 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
 
 /* Run exactly `iters` PCG iterations on the current level and state without
  * any stopping test (restart = 1 starts with beta = 0).  For step-by-step
- * comparison with a reference implementation. */
+ * comparison with a reference implementation.  opts->precision = GPSOC_MIXED
+ * runs the iterations in FP32 arrays (FP64 sums, scalars and step decisions,
+ * as in the FP32 phase of a mixed solve) from the FP64 state and writes the
+ * result back to it; restart = 0 continues the direction of the previous
+ * gpsoc_iterate call, which must then have used the same precision. */
 gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int restart,
                            gpsoc_result* results);
 
@@ -193,7 +210,10 @@ gpsoc_status gpsoc_get_psi_device(const gpsoc_problem* p, void* dptr);
 gpsoc_status gpsoc_get_observables(gpsoc_problem* p, double* E, double* mu, double* mass);
 
 /* Operator-level entry points (Sections 2.2, 3.1, 3.4) on the current level.
- * Host arrays as in gpsoc_set_initial.
+ * Host arrays as in gpsoc_set_initial.  precision = GPSOC_FP64 runs the FP64
+ * kernels; GPSOC_MIXED runs the FP32 kernels of the mixed-precision phase on an
+ * FP32 copy of the state (FP32 transforms and pointwise work, FP64 block and
+ * grid sums and scalars) and widens the array results to FP64.
  *   gpsoc_apply_h: H_l(Phi) of Eqs. eigen1-eigen3 for the current state into
  *     hpsi (may be NULL); obs (may be NULL) receives per solve 9 doubles:
  *     E, mu, alpha_1, alpha_0, alpha_-1 (Eq. PreCnstAlpha), mass_1, mass_0,
@@ -204,9 +224,9 @@ gpsoc_status gpsoc_get_observables(gpsoc_problem* p, double* E, double* mu, doub
  *     coefficients a_n, b_n (Eqs. an, bn; H_l(P) read with the density frozen at
  *     Phi) and the energy change E(cos t Phi + sin t P/||P||) - E(Phi) at
  *     n_theta angles theta[]; out receives per solve 2 + n_theta doubles. */
-gpsoc_status gpsoc_apply_h(gpsoc_problem* p, double* hpsi, double* obs);
-gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, const double* r, double* out);
-gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* theta, int n_theta,
+gpsoc_status gpsoc_apply_h(gpsoc_problem* p, int precision, double* hpsi, double* obs);
+gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, int precision, const double* r, double* out);
+gpsoc_status gpsoc_step_model(gpsoc_problem* p, int precision, const double* P, const double* theta, int n_theta,
                               double* out);
 
 /* Spectral zero-padding prolongation (Section 3.3, step c; read as zero
@@ -251,10 +271,21 @@ gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const 
 /* Retire, admit, launch (see above).  *busy (may be NULL) receives the number of
  * requests queued or running.  Not thread-safe: one caller per server. */
 gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy);
-/* GPSOC_OK with the result (and the final wave function in psi_out, may be NULL)
- * once the request finished -- the ticket is then released; GPSOC_ESTATE while it
- * is queued or running; GPSOC_EINVAL for an unknown ticket. */
-gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, gpsoc_result* res, double* psi_out);
+/* Result of one request.  timeout_ms = 0 only looks; timeout_ms > 0 drives the
+ * server (gpsoc_server_step) until the request finishes or timeout_ms have
+ * passed, waiting on the device in steps of at most that bound; timeout_ms < 0
+ * drives it until the request finishes.  Returns GPSOC_OK with the result (and
+ * the final wave function in psi_out, may be NULL) once the request finished --
+ * the ticket is then released; GPSOC_ETIMEOUT while it is still queued or
+ * running; GPSOC_EINVAL for an unknown ticket.  A cancelled request reports
+ * GPSOC_OK with res->status = GPSOC_ECANCELED and leaves psi_out untouched. */
+gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, int timeout_ms, gpsoc_result* res,
+                               double* psi_out);
+/* Withdraw a queued or running request.  A running solve is stopped on the device
+ * after the round in flight (stream-ordered) and its slot is freed at once; the
+ * ticket then polls as finished with status GPSOC_ECANCELED.  GPSOC_ESTATE if the
+ * request has already finished, GPSOC_EINVAL for an unknown ticket. */
+gpsoc_status gpsoc_server_cancel(gpsoc_server* s, uint64_t ticket);
 /* Device bytes reserved by buckets, number of buckets, queued requests. */
 gpsoc_status gpsoc_server_stats(const gpsoc_server* s, double* bytes_in_use, int* buckets, int* queued);
 
@@ -270,6 +301,13 @@ gpsoc_status gpsoc_server_stats(const gpsoc_server* s, double* bytes_in_use, int
 gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, double* ms, int cap, int* n_kernels);
 const char* gpsoc_profile_name(const gpsoc_problem* p, int k);
 uint64_t gpsoc_kernel_launches(const gpsoc_problem* p);
+/* Tile of the FFT passes along `axis` (0 = x rows, 1 = y, 2 = z columns) on
+ * multigrid level `level` for this problem's batch in the given precision:
+ * *lines = grid lines per thread block (rows for x, adjacent columns for y, z),
+ * *elems_per_thread = FFT elements per thread (the radix of the Stockham
+ * passes), *threads = threads per block. */
+gpsoc_status gpsoc_tile_shape(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
+                              int* elems_per_thread, int* threads);
 
 /* Arithmetic roofline probe (no counterpart in the paper): FP64 and FP32 FMA
  * throughput of the current device in TFLOP/s (an FMA counts 2 flops), from

@@ -710,6 +710,17 @@ static void col_cfg(const Geo& g, int axis, int nsolve, int& tc, int& ept, int& 
 }
 
 template <class T>
+void tile_shape(const Geo& g, int axis, int nsolve, int& lines, int& ept, int& threads) {
+  if (axis == 0) {
+    lines = row_rows_per_block<T>(g, nsolve);
+    ept = pick_ept<T>(3 * lines * g.n[0], g.n[0], false);
+    threads = round_threads(3 * lines * g.n[0] / ept);
+  } else {
+    col_cfg<T>(g, axis, nsolve, lines, ept, threads);
+  }
+}
+
+template <class T>
 int row_blocks_per_solve(const Geo& g, int nsolve) {
   return (int)(g.npts / g.n[0]) / row_rows_per_block<T>(g, nsolve);
 }
@@ -811,6 +822,8 @@ template void launch_row<double>(int, const ChainArgs<double>&, int, const Launc
 template void launch_row<float>(int, const ChainArgs<float>&, int, const Launch&, cudaStream_t);
 template void launch_col<double>(int, int, const ChainArgs<double>&, const Launch&, cudaStream_t);
 template void launch_col<float>(int, int, const ChainArgs<float>&, const Launch&, cudaStream_t);
+template void tile_shape<double>(const Geo&, int, int, int&, int&, int&);
+template void tile_shape<float>(const Geo&, int, int, int&, int&, int&);
 template int row_blocks_per_solve<double>(const Geo&, int);
 template int row_blocks_per_solve<float>(const Geo&, int);
 template int col_blocks_per_solve<double>(const Geo&, int, int);

@@ -8,11 +8,13 @@
 // only every `check_every` iterations.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "gpsoc_internal.cuh"
@@ -127,6 +129,8 @@ struct gpsoc_problem {
   std::vector<std::string> prof_names;
   std::vector<std::vector<int>> level_iters;   // per solve, iterations per level of the last solve
   std::vector<std::vector<int>> level_fp32;    // per solve, FP32 iterations per level of the last solve
+  std::vector<std::vector<double>> level_res32;   // per solve, max |r| where each level's FP32 phase ended
+  void* d_ptrs = nullptr;       // small device table of buffer pointers (FP32 phase hand-over)
 };
 
 namespace {
@@ -410,8 +414,8 @@ gpsoc_status enqueue_iteration(gpsoc_problem* p, int level, Bufs<T>& B, int pari
   gpsoc_status s = chain_args<T>(p, level, a);
   if (s != GPSOC_OK) return s;
   const Geo g = a.g;
-  a.sc = scalar_ctx<T>(p, g, o, fp32 ? 2 : 0);
   const int cur = parity & 1, prv = cur ^ 1;
+  a.sc = scalar_ctx<T>(p, g, o, (fp32 ? 2 : 0) | (cur << 2));
   // apply the pending step, H(Phi^n), E, mu, alpha
   run_h_chain<T>(p, a, B, B.Phi, B.HPhi, B.P[prv], 1);
   // r^n, stopping test, P_C r^n, beta
@@ -453,13 +457,14 @@ OptsDev make_opts(const gpsoc_opts* o) {
   d.max_halvings = o->max_halvings > 0 ? o->max_halvings : 40;
   d.no_stop = 0;
   d.precond = o->precond;
+  d.res32 = o->fp32_res_switch > 0 ? o->fp32_res_switch : 0.0;
   return d;
 }
 
-gpsoc_status init_level(gpsoc_problem* p, int level, bool reset_counters) {
+gpsoc_status init_level(gpsoc_problem* p, int level, bool reset_counters, bool keep_direction = false) {
   const Geo g = make_geo(p, level);
   ScalarArgs x = scalar_args(p, level, PH_INIT, g);
-  x.flags = reset_counters ? 1 : 0;
+  x.flags = (reset_counters ? 1 : 0) | (keep_direction ? 4 : 0);
   SL(p, x);
   CK(cudaGetLastError());
   return GPSOC_OK;
@@ -546,7 +551,7 @@ gpsoc_status convert_state(gpsoc_problem* p, int level, bool to32) {
 // fp32_rel * |E| or Algorithm 2 finds no decrease (the FP32 rounding floor),
 // then PCG in FP64 from that iterate (beta restarted) to the stopping rule.
 gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level,
-                       int precision, double fp32_rel) {
+                       int precision, double fp32_rel, bool carry) {
   gpsoc_status s;
   if (precision == GPSOC_MIXED) {
     s = ensure_fp32(p);
@@ -562,9 +567,22 @@ gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_
     o32.phase32 = 1;
     s = iterate_until_done<float>(p, level, o32, check_every);
     if (s != GPSOC_OK) return s;
-    s = convert_state(p, level, false);
-    if (s != GPSOC_OK) return s;
-    s = init_level(p, level, false);
+    for (int i = 0; i < p->batch; ++i) p->level_res32[i].push_back(p->h_st[i].res_inf);
+    // solves that took FP32 steps continue from their FP32 iterate and, unless the
+    // options ask for a restart, from its last direction (beta carried over)
+    {
+      const Geo g = make_geo(p, level);
+      const float2* r32[2] = {p->b32.R[0], p->b32.R[1]};
+      const float2* p32[2] = {p->b32.P[0], p->b32.P[1]};
+      float2** d_rp = reinterpret_cast<float2**>(p->d_ptrs);
+      CK(cudaMemcpyAsync(d_rp, r32, sizeof(r32), cudaMemcpyHostToDevice, p->stream));
+      CK(cudaMemcpyAsync(d_rp + 2, p32, sizeof(p32), cudaMemcpyHostToDevice, p->stream));
+      launch_handover(p->b32.Phi, d_rp, d_rp + 2, p->b64.Phi, p->b64.R[1], p->b64.P[1], p->d_st, 3 * g.npts, p->batch,
+                      carry ? 1 : 0, p->stream);
+      mark(p, "handover");
+      CK(cudaGetLastError());
+    }
+    s = init_level(p, level, false, carry);
     if (s != GPSOC_OK) return s;
     return iterate_until_done<double>(p, level, o, check_every);
   }
@@ -636,6 +654,7 @@ void fill_results(const gpsoc_problem* p, gpsoc_result* r, int levels) {
     for (int k = 0; k < 8; ++k) {
       o.level_iters[k] = (i < (int)p->level_iters.size() && k < (int)p->level_iters[i].size()) ? p->level_iters[i][k] : 0;
       o.level_fp32_iters[k] = (i < (int)p->level_fp32.size() && k < (int)p->level_fp32[i].size()) ? p->level_fp32[i][k] : 0;
+      o.level_res_fp32[k] = (i < (int)p->level_res32.size() && k < (int)p->level_res32[i].size()) ? p->level_res32[i][k] : 0.0;
     }
     o.status = S.status;
     if (S.status == GPSOC_OK && S.active) o.status = GPSOC_ENOTCONV;
@@ -659,18 +678,137 @@ gpsoc_status check_problem(const gpsoc_problem* p) {
   return GPSOC_OK;
 }
 
+// H chain + observables for the current state without touching iteration flags, in
+// the arrays of precision T (FP32: the FP64 state is first copied to the FP32 set;
+// sums and scalars stay FP64 in both)
+template <class T = double>
 gpsoc_status observables_now(gpsoc_problem* p) {
-  // H chain + observables for the current state without touching iteration flags
-  ChainArgs<double> a;
-  gpsoc_status s = chain_args<double>(p, p->level, a);
+  gpsoc_status s;
+  if constexpr (sizeof(T) == 4) {
+    s = ensure_fp32(p);
+    if (s != GPSOC_OK) return s;
+    s = convert_state(p, p->level, true);
+    if (s != GPSOC_OK) return s;
+  }
+  Bufs<T>& B = bufs<T>(p);
+  ChainArgs<T> a;
+  s = chain_args<T>(p, p->level, a);
   if (s != GPSOC_OK) return s;
   a.gate = GATE_ALL;
-  run_h_chain<double>(p, a, p->b64, p->b64.Phi, p->b64.HPhi);
-  ScalarArgs x = scalar_args(p, p->level, PH_OBS, a.g);
+  run_h_chain<T>(p, a, B, B.Phi, B.HPhi);
+  ScalarArgs x = scalar_args<T>(p, p->level, PH_OBS, a.g);
   x.force = 1;
   SL(p, x);
   CK(cudaGetLastError());
   return sync_state(p);
+}
+
+gpsoc_status check_precision(int precision) {
+  if (precision != GPSOC_FP64 && precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
+  return GPSOC_OK;
+}
+
+// device 3-array of precision T -> host FP64 (FP32 arrays are widened through the FP64 scratch D)
+template <class T>
+gpsoc_status copy_out(gpsoc_problem* p, const cx_t<T>* src, double* host) {
+  const Geo g = make_geo(p, p->level);
+  const long long cnt = (long long)p->batch * 3 * g.npts;
+  const double2* from = reinterpret_cast<const double2*>(src);
+  if constexpr (sizeof(T) == 4) {
+    launch_convert<double>(src, 1, p->b64.D, cnt, p->stream);
+    mark(p, "convert");
+    CK(cudaGetLastError());
+    from = p->b64.D;
+  }
+  CK(cudaMemcpyAsync(host, from, sizeof(double2) * (size_t)cnt, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
+}
+
+// host FP64 3-array -> device array of precision T (FP32: through the FP64 scratch D)
+template <class T>
+gpsoc_status copy_in(gpsoc_problem* p, const double* host, cx_t<T>* dst) {
+  const Geo g = make_geo(p, p->level);
+  const long long cnt = (long long)p->batch * 3 * g.npts;
+  double2* to = (sizeof(T) == 4) ? p->b64.D : reinterpret_cast<double2*>(dst);
+  CK(cudaMemcpyAsync(to, host, sizeof(double2) * (size_t)cnt, cudaMemcpyHostToDevice, p->stream));
+  if constexpr (sizeof(T) == 4) {
+    launch_convert<float>(p->b64.D, 0, dst, cnt, p->stream);
+    mark(p, "convert");
+    CK(cudaGetLastError());
+  }
+  return GPSOC_OK;
+}
+
+template <class T>
+gpsoc_status apply_h_impl(gpsoc_problem* p, double* hpsi, double* obs) {
+  gpsoc_status s = observables_now<T>(p);
+  if (s != GPSOC_OK) return s;
+  if (hpsi) {
+    s = copy_out<T>(p, bufs<T>(p).HPhi, hpsi);
+    if (s != GPSOC_OK) return s;
+  }
+  if (obs) {
+    for (int i = 0; i < p->batch; ++i) {
+      const SolveState& S = p->h_st[i];
+      double* o = obs + 9 * i;
+      o[0] = S.E; o[1] = S.mu;
+      for (int c = 0; c < 3; ++c) { o[2 + c] = S.alpha[c]; o[5 + c] = S.mass[c]; }
+      o[8] = S.Q;
+    }
+  }
+  return GPSOC_OK;
+}
+
+template <class T>
+gpsoc_status apply_precond_impl(gpsoc_problem* p, const double* r, double* out) {
+  gpsoc_status s = observables_now<T>(p);
+  if (s != GPSOC_OK) return s;
+  Bufs<T>& B = bufs<T>(p);
+  s = copy_in<T>(p, r, B.D);
+  if (s != GPSOC_OK) return s;
+  ChainArgs<T> a;
+  s = chain_args<T>(p, p->level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  a.given_r = 1;
+  run_pre_chain<T>(p, a, B, B.D, B.Phi, B.R[0], nullptr, B.Z, 0);
+  CK(cudaGetLastError());
+  return copy_out<T>(p, B.Z, out);
+}
+
+template <class T>
+gpsoc_status step_model_impl(gpsoc_problem* p, const double* P, const double* theta, int n_theta, double* out) {
+  gpsoc_status s = observables_now<T>(p);
+  if (s != GPSOC_OK) return s;
+  const Geo g = make_geo(p, p->level);
+  Bufs<T>& B = bufs<T>(p);
+  // the P chain forms P = -z + beta P_prev - cproj Phi: pass z = -P with beta = cproj = 0
+  std::vector<double> negP(2 * (size_t)p->batch * 3 * g.npts);
+  for (size_t i = 0; i < negP.size(); ++i) negP[i] = -P[i];
+  s = copy_in<T>(p, negP.data(), B.Z);
+  if (s != GPSOC_OK) return s;
+  double* d_theta = p->d_tmp;
+  double* d_out = p->d_tmp + n_theta;
+  if (n_theta) CK(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, p->stream));
+  // cproj = 0 so that P is used as given
+  for (int i = 0; i < p->batch; ++i) { p->h_st[i].cproj = 0.0; p->h_st[i].beta = 0.0; p->h_st[i].fcproj = 0.0f; p->h_st[i].fbeta = 0.0f; }
+  CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
+  ChainArgs<T> a;
+  s = chain_args<T>(p, p->level, a);
+  if (s != GPSOC_OK) return s;
+  a.gate = GATE_ALL;
+  run_p_chain<T>(p, a, B, B.Z, nullptr, B.Phi, B.HPhi, B.P[0], 0);
+  ScalarArgs x = scalar_args<T>(p, p->level, PH_MODEL, g);
+  x.force = 1;
+  x.thetas = d_theta;
+  x.n_theta = n_theta;
+  x.model_out = d_out;
+  SL(p, x);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, d_out, sizeof(double) * (size_t)p->batch * (2 + n_theta), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return GPSOC_OK;
 }
 
 }  // namespace
@@ -743,6 +881,7 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
   if (cudaMemset(p->d_st, 0, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ECUDA, "memset failed");
   if (cudaMallocHost(&p->h_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "host allocation failed");
   if (cudaMalloc(&p->d_scale, sizeof(double) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
+  if (cudaMalloc(&p->d_ptrs, 8 * sizeof(void*)) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
   p->tmp_len = (size_t)batch * 64 + 4096;
   if (cudaMalloc(&p->d_tmp, sizeof(double) * p->tmp_len) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");
   std::vector<PhysDev> ph(batch);
@@ -785,6 +924,7 @@ void gpsoc_destroy(gpsoc_problem* p) {
   if (p->d_cnt) cudaFree(p->d_cnt);
   if (p->h_st) cudaFreeHost(p->h_st);
   if (p->d_scale) cudaFree(p->d_scale);
+  if (p->d_ptrs) cudaFree(p->d_ptrs);
   if (p->d_tmp) cudaFree(p->d_tmp);
   if (p->d_phys) cudaFree(p->d_phys);
   if (p->d_userV) cudaFree(p->d_userV);
@@ -877,14 +1017,18 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
   gpsoc_status s = GPSOC_OK;
   p->level_iters.assign(p->batch, std::vector<int>());
   p->level_fp32.assign(p->batch, std::vector<int>());
+  p->level_res32.assign(p->batch, std::vector<double>());
   std::vector<int> done(p->batch, 0), done32(p->batch, 0);
   for (int lev = levels - 1; lev >= 0; --lev) {
     if (lev < p->level) {
       s = prolong_impl(p, lev + 1);
       if (s != GPSOC_OK) return s;
     }
-    s = run_level(p, lev, o, check, lev == levels - 1, level_precision(p, lev, opts),
-                  opts->fp32_switch > 0 ? opts->fp32_switch : 1e-10);
+    const int lp = level_precision(p, lev, opts);
+    s = run_level(p, lev, o, check, lev == levels - 1, lp, opts->fp32_switch > 0 ? opts->fp32_switch : 1e-10,
+                  opts->fp32_carry != 0);
+    if (lp != GPSOC_MIXED)
+      for (int i = 0; i < p->batch; ++i) p->level_res32[i].push_back(0.0);
     if (s != GPSOC_OK) return s;
     for (int i = 0; i < p->batch; ++i) {
       p->level_iters[i].push_back(p->h_st[i].total_iters - done[i]);
@@ -909,19 +1053,33 @@ gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   if (!opts || iters < 0) return fail(GPSOC_EINVAL, "bad arguments");
   if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  if (check_precision(opts->precision) != GPSOC_OK) return GPSOC_EINVAL;
   OptsDev o = make_opts(opts);
   o.no_stop = 1;
   gpsoc_status s;
+  const bool f32 = opts->precision == GPSOC_MIXED;
+  if (f32) {
+    // FP32 arrays (FP64 sums and scalars), from the FP64 state
+    s = ensure_fp32(p);
+    if (s == GPSOC_OK) s = convert_state(p, p->level, true);
+    if (s != GPSOC_OK) return s;
+  }
   if (restart) {
     s = init_level(p, p->level, true);
     if (s != GPSOC_OK) return s;
   }
   for (int k = 0; k < iters; ++k) {
-    s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
+    s = f32 ? enqueue_iteration<float>(p, p->level, p->b32, k & 1, o, 1)
+            : enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
     if (s != GPSOC_OK) return s;
   }
   if (iters > 0) {
-    s = flush_pending<double>(p, p->level, p->b64, (iters - 1) & 1);
+    s = f32 ? flush_pending<float>(p, p->level, p->b32, (iters - 1) & 1)
+            : flush_pending<double>(p, p->level, p->b64, (iters - 1) & 1);
+    if (s != GPSOC_OK) return s;
+  }
+  if (f32) {
+    s = convert_state(p, p->level, false);
     if (s != GPSOC_OK) return s;
   }
   s = sync_state(p);
@@ -964,89 +1122,33 @@ gpsoc_status gpsoc_get_observables(gpsoc_problem* p, double* E, double* mu, doub
   return GPSOC_OK;
 }
 
-gpsoc_status gpsoc_apply_h(gpsoc_problem* p, double* hpsi, double* obs) {
+gpsoc_status gpsoc_apply_h(gpsoc_problem* p, int precision, double* hpsi, double* obs) {
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (check_precision(precision) != GPSOC_OK) return GPSOC_EINVAL;
   if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
-  gpsoc_status s = observables_now(p);
-  if (s != GPSOC_OK) return s;
-  const Geo g = make_geo(p, p->level);
-  if (hpsi) {
-    CK(cudaMemcpyAsync(hpsi, p->b64.HPhi, sizeof(double2) * (size_t)p->batch * 3 * g.npts, cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
-  }
-  if (obs) {
-    for (int i = 0; i < p->batch; ++i) {
-      const SolveState& S = p->h_st[i];
-      double* o = obs + 9 * i;
-      o[0] = S.E; o[1] = S.mu;
-      for (int c = 0; c < 3; ++c) { o[2 + c] = S.alpha[c]; o[5 + c] = S.mass[c]; }
-      o[8] = S.Q;
-    }
-  }
-  return GPSOC_OK;
+  return precision == GPSOC_MIXED ? apply_h_impl<float>(p, hpsi, obs) : apply_h_impl<double>(p, hpsi, obs);
 }
 
-gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, const double* r, double* out) {
+gpsoc_status gpsoc_apply_precond(gpsoc_problem* p, int precision, const double* r, double* out) {
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!r || !out) return fail(GPSOC_EINVAL, "NULL argument");
+  if (check_precision(precision) != GPSOC_OK) return GPSOC_EINVAL;
   if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
-  gpsoc_status s = observables_now(p);
-  if (s != GPSOC_OK) return s;
-  const Geo g = make_geo(p, p->level);
-  const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
-  Bufs<double>& B = p->b64;
-  CK(cudaMemcpyAsync(B.D, r, bytes, cudaMemcpyHostToDevice, p->stream));
-  ChainArgs<double> a;
-  s = chain_args<double>(p, p->level, a);
-  if (s != GPSOC_OK) return s;
-  a.gate = GATE_ALL;
-  a.given_r = 1;
-  run_pre_chain<double>(p, a, B, B.D, B.Phi, B.R[0], nullptr, B.Z, 0);
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(out, B.Z, bytes, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
-  return GPSOC_OK;
+  return precision == GPSOC_MIXED ? apply_precond_impl<float>(p, r, out) : apply_precond_impl<double>(p, r, out);
 }
 
-gpsoc_status gpsoc_step_model(gpsoc_problem* p, const double* P, const double* theta, int n_theta, double* out) {
+gpsoc_status gpsoc_step_model(gpsoc_problem* p, int precision, const double* P, const double* theta, int n_theta,
+                              double* out) {
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!P || !out || n_theta < 0 || (n_theta > 0 && !theta)) return fail(GPSOC_EINVAL, "bad arguments");
+  if (check_precision(precision) != GPSOC_OK) return GPSOC_EINVAL;
   if (!p->has_state) return fail(GPSOC_ESTATE, "no state");
   if ((size_t)p->batch * (2 + n_theta) + n_theta > p->tmp_len) return fail(GPSOC_EINVAL, "too many angles");
-  gpsoc_status s = observables_now(p);
-  if (s != GPSOC_OK) return s;
-  const Geo g = make_geo(p, p->level);
-  const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
-  Bufs<double>& B = p->b64;
-  // the P chain forms P = -z + beta P_prev - cproj Phi: pass z = -P with beta = cproj = 0
-  std::vector<double> negP(2 * (size_t)p->batch * 3 * g.npts);
-  for (size_t i = 0; i < negP.size(); ++i) negP[i] = -P[i];
-  CK(cudaMemcpyAsync(B.Z, negP.data(), bytes, cudaMemcpyHostToDevice, p->stream));
-  double* d_theta = p->d_tmp;
-  double* d_out = p->d_tmp + n_theta;
-  if (n_theta) CK(cudaMemcpyAsync(d_theta, theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice, p->stream));
-  // cproj = 0 so that P is used as given
-  for (int i = 0; i < p->batch; ++i) { p->h_st[i].cproj = 0.0; p->h_st[i].beta = 0.0; p->h_st[i].fcproj = 0.0f; p->h_st[i].fbeta = 0.0f; }
-  CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
-  ChainArgs<double> a;
-  s = chain_args<double>(p, p->level, a);
-  if (s != GPSOC_OK) return s;
-  a.gate = GATE_ALL;
-  run_p_chain<double>(p, a, B, B.Z, nullptr, B.Phi, B.HPhi, B.P[0], 0);
-  CK(cudaStreamSynchronize(p->stream));
-  ScalarArgs x = scalar_args(p, p->level, PH_MODEL, g);
-  x.force = 1;
-  x.thetas = d_theta;
-  x.n_theta = n_theta;
-  x.model_out = d_out;
-  SL(p, x);
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(out, d_out, sizeof(double) * (size_t)p->batch * (2 + n_theta), cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
-  return GPSOC_OK;
+  return precision == GPSOC_MIXED ? step_model_impl<float>(p, P, theta, n_theta, out)
+                                  : step_model_impl<double>(p, P, theta, n_theta, out);
 }
 
 gpsoc_status gpsoc_prolong(gpsoc_problem* p, int level) {
@@ -1120,6 +1222,18 @@ const char* gpsoc_profile_name(const gpsoc_problem* p, int k) {
 }
 
 uint64_t gpsoc_kernel_launches(const gpsoc_problem* p) { return p ? p->launches : 0; }
+
+gpsoc_status gpsoc_tile_shape(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
+                              int* elems_per_thread, int* threads) {
+  g_err.clear();
+  if (!p || !lines || !elems_per_thread || !threads) return fail(GPSOC_EINVAL, "NULL argument");
+  if (level < 0 || level > p->max_level || axis < 0 || axis >= p->dim) return fail(GPSOC_EINVAL, "bad level or axis");
+  if (check_precision(precision) != GPSOC_OK) return GPSOC_EINVAL;
+  const Geo g = make_geo(p, level);
+  if (precision == GPSOC_MIXED) tile_shape<float>(g, axis, p->batch, *lines, *elems_per_thread, *threads);
+  else tile_shape<double>(g, axis, p->batch, *lines, *elems_per_thread, *threads);
+  return GPSOC_OK;
+}
 
 gpsoc_status gpsoc_fft_axis(gpsoc_problem* p, void* data, int count, int axis, int inverse) {
   g_err.clear();
@@ -1378,9 +1492,17 @@ gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const 
   return GPSOC_OK;
 }
 
-gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
-  g_err.clear();
-  if (!s) return fail(GPSOC_EINVAL, "NULL server");
+}  // extern "C"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// One server step (retire, admit, launch).  If no round has finished it waits
+// for the earliest-launched one: without limit when `bounded` is false, else
+// until `deadline`, after which it goes on to admission and launches without
+// retiring anything.
+gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::time_point deadline) {
   gpsoc_status err = GPSOC_OK;
   // 1. buckets whose round of iterations finished: retire the solves that stopped.
   //    If no bucket has finished yet, wait for the one launched first.
@@ -1393,7 +1515,19 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
     if (q != cudaErrorNotReady) return fail(GPSOC_ECUDA, std::string("bucket event: ") + cudaGetErrorString(q));
     if (!oldest || b->launched < oldest->launched) oldest = b;
   }
-  if (!any_done && oldest) CK(cudaEventSynchronize(oldest->done));
+  if (!any_done && oldest) {
+    if (!bounded) {
+      CK(cudaEventSynchronize(oldest->done));
+    } else {
+      for (;;) {
+        const cudaError_t q = cudaEventQuery(oldest->done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(GPSOC_ECUDA, std::string("bucket event: ") + cudaGetErrorString(q));
+        if (Clock::now() >= deadline) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+      }
+    }
+  }
   for (Bucket* b : s->buckets) {
     if (!b->in_flight || cudaEventQuery(b->done) != cudaSuccess) continue;
     b->in_flight = false;
@@ -1470,17 +1604,69 @@ gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
   return GPSOC_OK;
 }
 
-gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, gpsoc_result* res, double* psi_out) {
+}  // namespace
+
+extern "C" {
+
+gpsoc_status gpsoc_server_step(gpsoc_server* s, int* busy) {
+  g_err.clear();
+  if (!s) return fail(GPSOC_EINVAL, "NULL server");
+  return server_step_impl(s, busy, false, Clock::now());
+}
+
+gpsoc_status gpsoc_server_poll(gpsoc_server* s, uint64_t ticket, int timeout_ms, gpsoc_result* res, double* psi_out) {
   g_err.clear();
   if (!s) return fail(GPSOC_EINVAL, "NULL server");
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return fail(GPSOC_EINVAL, "unknown ticket");
   ServerReq* r = it->second;
-  if (r->stage != 3) return GPSOC_ESTATE;   // still queued or running (no message: polling is routine)
+  if (r->stage != 3 && timeout_ms != 0) {
+    // drive the server until this request finishes or the wait runs out
+    const bool bounded = timeout_ms > 0;
+    const Clock::time_point deadline = Clock::now() + std::chrono::milliseconds(bounded ? timeout_ms : 0);
+    while (r->stage != 3) {
+      if (bounded && Clock::now() >= deadline) break;
+      int busy = 0;
+      const gpsoc_status st = server_step_impl(s, &busy, bounded, deadline);
+      if (st != GPSOC_OK) return st;
+      if (busy == 0 && r->stage != 3) return fail(GPSOC_ESTATE, "request neither queued nor running");
+    }
+  }
+  if (r->stage != 3) return GPSOC_ETIMEOUT;   // still queued or running (no message: polling is routine)
   if (res) *res = r->res;
-  if (psi_out) std::memcpy(psi_out, r->psi.data(), sizeof(double) * r->psi.size());
+  if (psi_out && r->res.status != GPSOC_ECANCELED) std::memcpy(psi_out, r->psi.data(), sizeof(double) * r->psi.size());
   delete r;
   s->reqs.erase(it);
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_server_cancel(gpsoc_server* s, uint64_t ticket) {
+  g_err.clear();
+  if (!s) return fail(GPSOC_EINVAL, "NULL server");
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return fail(GPSOC_EINVAL, "unknown ticket");
+  ServerReq* r = it->second;
+  if (r->stage == 3) return fail(GPSOC_ESTATE, "request already finished");
+  bool found = false;
+  for (size_t q = 0; q < s->queue.size(); ++q) {
+    if (s->queue[q] == ticket) { s->queue.erase(s->queue.begin() + q); found = true; break; }
+  }
+  for (Bucket* b : s->buckets) {
+    if (found) break;
+    for (size_t k = 0; k < b->slot.size(); ++k) {
+      if (b->slot[k] != (int64_t)ticket) continue;
+      // stop the slot's solve on the device, stream-ordered after any round in flight;
+      // the slot is free for admission at once (a later load is ordered after this too)
+      CK(cudaMemsetAsync(&b->p->d_st[k].active, 0, sizeof(int), b->p->stream));
+      b->slot[k] = -1;
+      found = true;
+      break;
+    }
+  }
+  if (!found) return fail(GPSOC_ESTATE, "request neither queued nor running");
+  r->res = gpsoc_result{};
+  r->res.status = GPSOC_ECANCELED;
+  r->stage = 3;
   return GPSOC_OK;
 }
 

@@ -84,6 +84,7 @@ struct SolveState {
   int fp32_iters, fp64_iters;
   int pending;      // an accepted step waits to be applied by the next iteration's first pass
   int it_win;       // FP32 phase: iteration at which the current stall window opened
+  int last_par;     // buffer parity (0/1) of the iteration whose step was accepted last
   // observables of the current iterate
   double E, mu, Q;          // energy, chemical potential, <H_lin Phi, Phi>
   double rho2, F2;          // sum rho^2, sum |F|^2 (times dV)
@@ -116,6 +117,7 @@ struct OptsDev {
   int phase32;      // FP32 phase of a mixed solve: stagnation / iteration cap end the phase, not the solve
   double tol_rel;   // energy stop: |dE| < tol + tol_rel * |E|
   int precond;      // GPSOC_PRECOND_*
+  double res32;     // FP32 phase: ends (or never starts) once max |r| < res32 (0 = no residual rule)
 };
 
 // reduction slots (per solve); partial sums live in part[(s * NSLOT + slot) * pmax + block]
@@ -150,7 +152,7 @@ struct ScalarCtx {
   long long npts;
   double dV;
   OptsDev opts;
-  int flags;            // 2 = count accepted steps as FP32 iterations
+  int flags;            // 2 = count accepted steps as FP32 iterations; bit 2 = buffer parity of the iteration
   double inv_npts;      // 1 / npts
 };
 
@@ -440,5 +442,9 @@ template <class T>
 int col_blocks_per_solve(const Geo& g, int axis, int nsolve);
 template <class T>
 cudaError_t chain_prepare();   // sets max dynamic shared memory attributes
+// tile of the axis passes: lines per tile (rows R for axis 0, columns TC otherwise),
+// FFT elements per thread and threads per block, for a launch over nsolve solves
+template <class T>
+void tile_shape(const Geo& g, int axis, int nsolve, int& lines, int& ept, int& threads);
 
 }  // namespace gpsoc

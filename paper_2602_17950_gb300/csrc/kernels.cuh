@@ -25,7 +25,7 @@ struct ScalarArgs {
   int nb_row, nb_col;
   int nsolve;
   int phase;
-  int flags;          // PH_INIT: 1 = reset counters; PH_STEP: 2 = count as an FP32 iteration
+  int flags;          // PH_INIT: 1 = reset counters, 4 = keep the direction; PH_STEP: 2 = count as an FP32 iteration
   long long npts;
   double dV;
   OptsDev opts;
@@ -60,6 +60,9 @@ void launch_scalar(const ScalarArgs& a, cudaStream_t st);
 template <class T> void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st);
 template <class T> void launch_pad(const cx_t<T>* in, cx_t<T>* out, const Geo& gc, const Geo& gf, int nsolve, cudaStream_t st);
 template <class T> void launch_convert(const void* in, int in_fp32, cx_t<T>* out, long long count, cudaStream_t st);
+void launch_handover(const float2* phi32, const float2* const* r32, const float2* const* p32, double2* phi64,
+                     double2* r64_prev, double2* p64_prev, const SolveState* st, long long per_solve, int nsolve,
+                     int carry, cudaStream_t stream);
 void launch_guess(double2* out, const Geo& g, const TrapDev& trap, const PhysDev* phys, int nsolve, const int kind[3],
                   double muTF_base, double* mass_tmp, cudaStream_t st);
 

@@ -87,7 +87,11 @@ extern "C" gpsoc_status gpsoc_apply_h_noalloc(const gpsoc_grid* grid, const gpso
                                               void* d_hpsi, double* obs, void* cuda_stream) {
   if (!grid || !trap || !params || !d_psi || !d_hpsi || batch < 1) return GPSOC_EINVAL;
   if (grid->dim != 2 && grid->dim != 3) return GPSOC_EINVAL;
-  if (trap->kind == GPSOC_TRAP_USER) return GPSOC_EINVAL;
+  // the same trap checks as gpsoc_create; user potentials would need device memory of their own
+  if (trap->kind != GPSOC_TRAP_HARMONIC && trap->kind != GPSOC_TRAP_HARMONIC_QUARTIC) return GPSOC_EINVAL;
+  for (int i = 0; i < grid->dim; ++i)
+    if (!std::isfinite(trap->g[i])) return GPSOC_EINVAL;
+  if (!std::isfinite(trap->quad) || !std::isfinite(trap->quart)) return GPSOC_EINVAL;
   Geo g{};
   g.d = grid->dim;
   g.npts = 1;

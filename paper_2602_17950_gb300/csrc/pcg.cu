@@ -29,7 +29,10 @@ __global__ void k_scalar(ScalarArgs A) {
   switch (ph_) {
     case PH_INIT:
       if (threadIdx.x == 0) {
-        S.active = 1; S.status = GPSOC_OK; S.iters = 0; S.first = 1; S.reset = 0; S.pending = 0;
+        // flags & 4: the level continues from a direction handed over by the FP32 phase
+        // (first, s_prev and the stored r_prev, P_prev are kept)
+        if (!(A.flags & 4)) S.first = 1;
+        S.active = 1; S.status = GPSOC_OK; S.iters = 0; S.reset = 0; S.pending = 0;
         S.dE_last = nan(""); S.dphi_inf = nan(""); S.E_win = INFINITY; S.it_win = 0;
         if (A.flags & 1) { S.total_iters = 0; S.beta_resets = 0; S.halvings = 0; S.fp32_iters = 0; S.fp64_iters = 0; }
         mirror32(S);
@@ -184,6 +187,28 @@ __global__ void k_pad(const cx_t<T>* in, cx_t<T>* out, Geo gc, Geo gf, int nsolv
   }
 }
 
+// End of an FP32 phase: solves that took FP32 steps get their state back in FP64
+// (Phi, and r_prev, P_prev of the last accepted step into the FP64 buffers of parity 1,
+// which the first FP64 iteration reads as the previous ones); a solve that took no
+// FP32 step keeps its FP64 state untouched.
+__global__ void k_handover(const float2* phi32, const float2* const* r32, const float2* const* p32, double2* phi64,
+                           double2* r64_prev, double2* p64_prev, const SolveState* st, long long per_solve,
+                           int nsolve, int carry) {
+  const long long tot = (long long)nsolve * per_solve;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(i / per_solve);
+    const SolveState& S = st[s];
+    if (S.iters == 0) continue;
+    const float2 f = phi32[i];
+    phi64[i] = make_double2(f.x, f.y);
+    if (carry && !S.first) {
+      const float2 r = r32[S.last_par][i], q = p32[S.last_par][i];
+      r64_prev[i] = make_double2(r.x, r.y);
+      p64_prev[i] = make_double2(q.x, q.y);
+    }
+  }
+}
+
 template <class T>
 __global__ void k_convert(const void* in, int in_fp32, cx_t<T>* out, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
@@ -285,6 +310,12 @@ void launch_pad(const cx_t<T>* in, cx_t<T>* out, const Geo& gc, const Geo& gf, i
 template <class T>
 void launch_convert(const void* in, int in_fp32, cx_t<T>* out, long long count, cudaStream_t st) {
   k_convert<T><<<1024, 256, 0, st>>>(in, in_fp32, out, count);
+}
+
+void launch_handover(const float2* phi32, const float2* const* r32, const float2* const* p32, double2* phi64,
+                     double2* r64_prev, double2* p64_prev, const SolveState* st, long long per_solve, int nsolve,
+                     int carry, cudaStream_t stream) {
+  k_handover<<<1024, 256, 0, stream>>>(phi32, r32, p32, phi64, r64_prev, p64_prev, st, per_solve, nsolve, carry);
 }
 
 void launch_guess(double2* out, const Geo& g, const TrapDev& trap, const PhysDev* phys, int nsolve, const int kind[3],

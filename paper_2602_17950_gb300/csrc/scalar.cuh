@@ -112,6 +112,10 @@ __device__ __forceinline__ void sc_res(const ScalarCtx& X, int s, double* scratc
   S.res_inf = rinf;
   if (!isfinite(rinf)) { deactivate(S, GPSOC_ENONFINITE); return; }
   if (O.no_stop) return;
+  // FP32 phase: once the residual is this small the FP32 rounding floor is near, so
+  // the level continues in FP64 (also at iteration 0: a level that starts converged
+  // takes no FP32 step)
+  if (O.phase32 && O.res32 > 0.0 && rinf < O.res32) { S.active = 0; return; }
   if (S.iters >= 1 || O.stop == GPSOC_STOP_RES) {
     bool conv;
     if (O.stop == GPSOC_STOP_ENERGY) conv = fabs(S.dE_last) < O.tol + O.tol_rel * fabs(S.E);
@@ -277,6 +281,7 @@ __device__ __forceinline__ void step_decide(const ScalarCtx& X, int s, SolveStat
   const double nrm2 = cs * cs * M + 2.0 * cs * sp * S.RPhi + sp * sp * S.P2;
   S.upd_c = cs; S.upd_s = sp; S.upd_scale = rsqrt(nrm2);
   S.pending = 1;
+  S.last_par = (X.flags >> 2) & 1;
   S.iters++; S.total_iters++;
   if (X.flags & 2) S.fp32_iters++; else S.fp64_iters++;
   S.first = 0;

@@ -16,7 +16,7 @@ GPSOC_FP64, GPSOC_MIXED = 0, 1
 GPSOC_STOP_DPHI, GPSOC_STOP_RES, GPSOC_STOP_ENERGY = 1, 2, 3
 TRAP_HARMONIC, TRAP_HARMONIC_QUARTIC, TRAP_USER = 0, 1, 2
 _STATUS = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ENONFINITE", "ETIMEOUT", "ESTATE", "EBUDGET",
-           "ESTAGNATED"]
+           "ESTAGNATED", "ECANCELED"]
 
 
 def status_name(code: int) -> str:
@@ -50,14 +50,16 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("stop", C.c_int), ("tol", C.c_double), ("res_tol", C.c_double),
                 ("max_iter", C.c_int), ("theta_trial", C.c_double), ("sigma", C.c_double),
                 ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int),
-                ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int), ("precond", C.c_int)]
+                ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int), ("precond", C.c_int),
+                ("fp32_res_switch", C.c_double), ("fp32_carry", C.c_int)]
 
 
 class Result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("total_iters", C.c_int), ("levels", C.c_int),
                 ("beta_resets", C.c_int), ("halvings", C.c_int), ("fp32_iters", C.c_int), ("fp64_iters", C.c_int),
                 ("energy", C.c_double), ("mu", C.c_double), ("mass", C.c_double * 3), ("res_inf", C.c_double),
-                ("dE_last", C.c_double), ("level_iters", C.c_int * 8), ("level_fp32_iters", C.c_int * 8)]
+                ("dE_last", C.c_double), ("level_iters", C.c_int * 8), ("level_fp32_iters", C.c_int * 8),
+                ("level_res_fp32", C.c_double * 8)]
 
     def as_dict(self):
         return {"status": status_name(self.status), "iters": self.iters, "total_iters": self.total_iters,
@@ -65,7 +67,8 @@ class Result(C.Structure):
                 "fp32_iters": self.fp32_iters, "fp64_iters": self.fp64_iters, "energy": self.energy,
                 "mu": self.mu, "mass": list(self.mass), "res_inf": self.res_inf, "dE_last": self.dE_last,
                 "level_iters": list(self.level_iters[:max(self.levels, 1)]),
-                "level_fp32_iters": list(self.level_fp32_iters[:max(self.levels, 1)])}
+                "level_fp32_iters": list(self.level_fp32_iters[:max(self.levels, 1)]),
+                "level_res_fp32": list(self.level_res_fp32[:max(self.levels, 1)])}
 
 
 class ServerOpts(C.Structure):
@@ -88,14 +91,16 @@ _PROTOS = {
     "gpsoc_get_psi": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gpsoc_get_psi_device": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gpsoc_get_observables": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
-    "gpsoc_apply_h": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
-    "gpsoc_apply_precond": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
-    "gpsoc_step_model": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "gpsoc_apply_h": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "gpsoc_apply_precond": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "gpsoc_step_model": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "gpsoc_prolong": (C.c_int, [C.c_void_p, C.c_int]),
     "gpsoc_fft_axis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "gpsoc_profile": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "gpsoc_profile_name": (C.c_char_p, [C.c_void_p, C.c_int]),
     "gpsoc_kernel_launches": (C.c_uint64, [C.c_void_p]),
+    "gpsoc_tile_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
     "gpsoc_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gpsoc_apply_h_noalloc": (C.c_int, [C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_int, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -104,7 +109,8 @@ _PROTOS = {
     "gpsoc_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_void_p,
                                       C.POINTER(Opts), C.POINTER(C.c_uint64)]),
     "gpsoc_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
-    "gpsoc_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result), C.c_void_p]),
+    "gpsoc_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(Result), C.c_void_p]),
+    "gpsoc_server_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "gpsoc_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "gpsoc_last_error": (C.c_char_p, []),
     "gpsoc_version": (C.c_char_p, []),
@@ -230,10 +236,10 @@ class Problem:
     @staticmethod
     def opts(precision=GPSOC_FP64, stop=GPSOC_STOP_ENERGY, tol=1e-12, res_tol=0.0, max_iter=100000,
              theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0, fp32_switch=0.0,
-             fp32_min_points=0, precond="combined"):
+             fp32_min_points=0, precond="combined", fp32_res_switch=0.0, fp32_carry=0):
         pk = PRECONDS.index(precond) if isinstance(precond, str) else int(precond)
         return Opts(precision, stop, tol, res_tol, max_iter, theta_trial, sigma, max_halvings, cm_levels,
-                    check_every, fp32_switch, fp32_min_points, pk)
+                    check_every, fp32_switch, fp32_min_points, pk, fp32_res_switch, int(fp32_carry))
 
     # -------------------------------------------------------------- state
     def set_initial(self, psi: np.ndarray, level=0):
@@ -285,23 +291,24 @@ class Problem:
         return [r.as_dict() for r in res]
 
     # -------------------------------------------------------------- operators
-    def apply_h(self):
+    def apply_h(self, precision=GPSOC_FP64):
+        """H_l(Phi) and 9 observables per solve; precision=GPSOC_MIXED runs the FP32 kernels."""
         hp = np.empty(self.shape(), dtype=np.complex128)
         obs = np.empty((self.batch, 9))
-        _check(library().gpsoc_apply_h(self._h, _ptr(hp), _ptr(obs)))
+        _check(library().gpsoc_apply_h(self._h, int(precision), _ptr(hp), _ptr(obs)))
         return hp, obs
 
-    def apply_precond(self, r: np.ndarray):
+    def apply_precond(self, r: np.ndarray, precision=GPSOC_FP64):
         r = np.ascontiguousarray(r, dtype=np.complex128).reshape(self.shape())
         out = np.empty_like(r)
-        _check(library().gpsoc_apply_precond(self._h, _ptr(r), _ptr(out)))
+        _check(library().gpsoc_apply_precond(self._h, int(precision), _ptr(r), _ptr(out)))
         return out
 
-    def step_model(self, P: np.ndarray, thetas):
+    def step_model(self, P: np.ndarray, thetas, precision=GPSOC_FP64):
         P = np.ascontiguousarray(P, dtype=np.complex128).reshape(self.shape())
         th = np.ascontiguousarray(thetas, dtype=np.float64)
         out = np.empty((self.batch, 2 + th.size))
-        _check(library().gpsoc_step_model(self._h, _ptr(P), _ptr(th), th.size, _ptr(out)))
+        _check(library().gpsoc_step_model(self._h, int(precision), _ptr(P), _ptr(th), th.size, _ptr(out)))
         return out
 
     def prolong(self):
@@ -319,6 +326,13 @@ class Problem:
 
     def kernel_launches(self) -> int:
         return int(library().gpsoc_kernel_launches(self._h))
+
+    def tile_shape(self, axis, level=0, precision=GPSOC_FP64):
+        """(lines per tile, FFT elements per thread, threads) of the passes along `axis`."""
+        a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(library().gpsoc_tile_shape(self._h, int(level), int(axis), int(precision), C.byref(a), C.byref(b),
+                                          C.byref(c)))
+        return a.value, b.value, c.value
 
     def fft_axis(self, data_dptr: int, count: int, axis: int, inverse=False):
         _check(library().gpsoc_fft_axis(self._h, C.c_void_p(data_dptr), count, axis, int(inverse)))
@@ -377,18 +391,24 @@ class Server:
         _check(library().gpsoc_server_step(self._h, C.byref(busy)))
         return busy.value
 
-    def poll(self, ticket, want_psi=True):
-        """(result dict, psi) once finished, else None."""
+    def poll(self, ticket, want_psi=True, timeout_ms=0):
+        """(result dict, psi) once finished, else None.  timeout_ms > 0 drives the server
+        until the request finishes or the time runs out; < 0 waits without limit."""
         res = Result()
         shape = self._shapes.get(ticket)    # unknown tickets are rejected by the library
         psi = np.empty(shape, dtype=np.complex128) if want_psi and shape is not None else None
-        code = library().gpsoc_server_poll(self._h, C.c_uint64(ticket), C.byref(res),
+        code = library().gpsoc_server_poll(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(res),
                                            _ptr(psi) if psi is not None else None)
-        if code == 7:
+        if code == 6:                    # ETIMEOUT: still queued or running
             return None
         _check(code)
         self._shapes.pop(ticket, None)
+        if res.status == 10:             # ECANCELED: no wave function
+            psi = None
         return res.as_dict(), psi
+
+    def cancel(self, ticket):
+        _check(library().gpsoc_server_cancel(self._h, C.c_uint64(ticket)))
 
     def stats(self):
         b = C.c_double(0)

@@ -39,7 +39,7 @@ def test_struct_sizes_match_c_layout():
     from paper_2602_17950_gb300 import gpsoc as g
     assert ctypes.sizeof(g.Grid) == 4 + 12 + 24              # int, int[3], double[3]
     assert ctypes.sizeof(g.Params) == 32
-    assert ctypes.sizeof(g.Result) == 8 * 4 + 8 * 7 + 4 * 8 + 4 * 8
+    assert ctypes.sizeof(g.Result) == 8 * 4 + 8 * 7 + 4 * 8 + 4 * 8 + 8 * 8
 
 
 def test_version_and_error_without_gpu(lib):

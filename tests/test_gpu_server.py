@@ -108,3 +108,30 @@ def test_poll_states():
         assert sv.poll(t) is None        # queued
         with pytest.raises(GpsocError, match="EINVAL"):
             sv.poll(t + 1000)
+
+
+def test_cancel_and_bounded_poll():
+    from paper_2602_17950_gb300 import GpsocError, Problem, Server
+    n, L = (64, 64), (8.0, 8.0)
+    pars = [(0.5, 0.5, 100.0, -1.0), (0.3, 0.8, 60.0, 2.0), (0.4, 0.2, 80.0, -2.0)]
+    psis = [si.gaussian_guess(n, L, 450 + k) for k in range(3)]
+    opts = dict(tol=1e-13, res_tol=1e-10)
+    with Server(hbm_budget_bytes=1e9, slots_per_bucket=1, precision=0, iters_per_step=8) as sv:
+        t = [sv.submit(n, L, pars[k], psis[k], trap=TRAP, **opts) for k in range(3)]
+        sv.cancel(t[2])                               # still queued
+        sv.step()                                     # t[0] admitted and running, t[1] queued
+        sv.cancel(t[0])                               # running: stopped after its round, slot freed
+        for k in (0, 2):
+            r, psi = sv.poll(t[k])
+            assert r["status"] == "ECANCELED" and psi is None
+        with pytest.raises(GpsocError, match="EINVAL"):
+            sv.cancel(t[0])                           # released ticket
+        assert sv.poll(t[1], timeout_ms=1) is None    # a bounded wait that runs out: ETIMEOUT
+        got = sv.poll(t[1], timeout_ms=-1)            # wait until it finishes
+        assert got is not None
+        r, psi = got
+    with Problem(n, L, [pars[1]], trap=TRAP) as p:
+        p.set_initial(psis[1][None])
+        ra = p.solve(**opts)[0]
+    assert r["status"] == "OK" and ra["status"] == "OK"
+    assert r["energy"] == pytest.approx(ra["energy"], rel=1e-10)

@@ -32,12 +32,16 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("n,L", [((64, 64), (8.0, 8.0)), ((32, 64), (6.0, 9.0)), ((16, 16, 32), (4.0, 4.0, 5.0))])
-def test_noalloc_apply_h_matches_allocating_entry_point(n, L):
+@pytest.mark.parametrize("n,L,batch", [((64, 64), (8.0, 8.0), 2), ((32, 64), (6.0, 9.0), 2),
+                                       ((16, 16, 32), (4.0, 4.0, 5.0), 2),
+                                       ((32, 32), (6.0, 6.0), 40)])     # 4 rows / 4 columns per tile
+def test_noalloc_apply_h_matches_allocating_entry_point(n, L, batch):
+    from oracle.model import Grid, Model, Trap
     from paper_2602_17950_gb300 import Problem, gpsoc
-    pars = [(0.45, 0.8, 30.0, -4.0), (0.9, 0.2, 120.0, 2.0)]
+    base = [(0.45, 0.8, 30.0, -4.0), (0.9, 0.2, 120.0, 2.0)]
+    pars = [base[k % 2] for k in range(batch)]
     trap = {"kind": 1, "g": (1.0, 1.3, 0.7), "quad": -0.1, "quart": 0.02}
-    psi = np.stack([si.smooth_random_state(n, L, 70 + k, width=min(L) / 3) for k in range(2)])
+    psi = np.stack([si.smooth_random_state(n, L, 70 + k, width=min(L) / 3) for k in range(batch)])
     with Problem(n, L, pars, trap=trap) as p:
         p.set_initial(psi)
         ref_h, ref_obs = p.apply_h()
@@ -47,9 +51,15 @@ def test_noalloc_apply_h_matches_allocating_entry_point(n, L):
         d_out = torch.full_like(d_psi, float("nan"))
         obs = gpsoc.apply_h_noalloc(n, L, pars, trap, d_psi.data_ptr(), d_out.data_ptr())
         got = d_out.cpu().numpy()
-        for k in range(2):
+        for k in range(batch):
             assert rel_max(got[k], ref_h[k]) < 1e-11
             np.testing.assert_allclose(obs[k], ref_obs[k], rtol=1e-12, atol=1e-15)
+    # and against the CPU oracle's H(Phi) (Eqs. eigen1-eigen3) for two of the solves
+    for k in (0, batch - 1):
+        m = Model(Grid(n, L), Trap(g=trap["g"], quad=trap["quad"], quart=trap["quart"]), Omega=pars[k][0],
+                  gamma=pars[k][1], c0=pars[k][2], c1=pars[k][3])
+        assert rel_max(got[k], m.H(phi[k])) < 1e-11
+        assert obs[k, 0] == pytest.approx(m.energy(phi[k]), rel=1e-12)
 
 
 def test_noalloc_rejects_oversized_problem():
