@@ -130,12 +130,27 @@ KERNEL_WORK = {
     "row_inv_pre": (1, "row", 5), "el_dir": (0, "row", 4), "row_fwd_proj": (1, "row", 5),
     "row_inv_p": (2, "row", 5),
 }
+# Hybrid iteration (FP64 state, FP32 directions): algorithmic bytes per grid point and
+# component of each pass (FP64 complex 16 B, FP32 complex 8 B; every array read or
+# written once).  hy_upd: R Phi, H_lin Phi (FP64), P, H_lin P (FP32); W Phi, H_lin Phi,
+# FP32 Phi.  row_fwd_pre_hy: R Phi, H_lin Phi; W r, F_x(P_V^1/2 r).  coly_ymid_h in the
+# hybrid P chain also reads and writes the spectra of Phi and P.  row_inv_p_hy: R T', G,
+# P, FP32 Phi, r, FP64 Phi; W H_lin P.
+HYBRID_BYTES = {"hy_upd": 88, "row_fwd_pre_hy": 48, "coly_mid_pre": 16, "row_inv_pre": 40, "el_dir": 32,
+                "row_fwd_proj": 40, "coly_ymid_h": 56, "row_inv_p_hy": 64}
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu
 # on the kernel inside this workload: (kernel, grid points per axis, 1 = FP32 / 0 = FP64).
 # At 128^2 the arrays stay in L2 (0 bytes written back during the launch).
 NCU_DRAM_BYTES = {("coly_ymid_h", 128, 0): 869888.0}
+
+
+def launch_bytes(name: str, n, prec: int) -> float:
+    """Algorithmic bytes of one launch on one solve in the given precision mode."""
+    if prec == 2:
+        return HYBRID_BYTES.get(name, 0) * 3.0 * n[0] * n[1]
+    return kernel_bytes(name, n, 8 if prec == 1 else 16)
 
 
 def kernel_flops(name: str, n) -> float:
@@ -274,7 +289,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    prec = 1 if args.precision == "mixed" else 0
+    prec = {"fp64": 0, "mixed": 1, "hybrid": 2}[args.precision]
     psi0 = initial_guess(rank)
     d_psi0 = torch.from_numpy(psi0[None].copy()).to(dev)
     flush = torch.empty(L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -299,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
 
     # the plain FP64 PCG on the same workload and tolerance (the comparison of the metric)
     fp64 = None
-    if prec == 1 and not args.no_fp64:
+    if prec != 0 and not args.no_fp64:
         lat64, res64 = timed_solves(prob, dict(opts, precision=0), d_psi0, flush, stream, 1, args.fp64_steps, torch)
         fp64 = {"value": world * 1000.0 / statistics.mean(lat64), "unit": "solves/s",
                 "ms_per_solve": statistics.mean(lat64), "p50_ms": float(np.percentile(lat64, 50)),
@@ -332,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
         n = tuple(k >> (LEVELS - 1 - lev) for k in N_FINE)
         its32 = fp32_lv[lev]
         its64 = last["level_iters"][lev] - its32
-        for pr, its in ((1, its32), (0, its64)):
+        for pr, its in ((prec if prec else 1, its32), (0, its64)):
             if its <= 0:
                 continue
             with Problem(n, L_BOX, [PAR]) as pl:
@@ -353,7 +368,13 @@ def run_ours(args, rank, world, local_rank):
     dom_ms = statistics.mean([ms for name, ms in prof[(dom_n, dom_pr)][1] if name == dom_name])
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else 6800.0
-    if dom_pr == 1:
+    if dom_pr == 2:
+        by = HYBRID_BYTES.get(dom_name, 0) * 3.0 * dom_n * dom_n
+        achieved = by / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{dom_name} @ {dom_n}^2 (hybrid)", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "algorithmic_bytes_per_launch": by}
+    elif dom_pr == 1:
         by = kernel_bytes(dom_name, (dom_n, dom_n), 8)
         achieved = by / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": f"{dom_name} @ {dom_n}^2 (FP32)", "achieved": achieved,
@@ -375,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+        "dtype": "f32+f64" if prec else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "solves_per_step_per_gpu": 1,
                    "grid": "512x512", "levels": [128, 256, 512], "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
@@ -521,7 +542,8 @@ def serve_trace_run(requests, rate, tol, res_tol, arms, max_iter, hbm_budget, sl
            "grid_mix": {f"{'x'.join(map(str, n))}": sum(q["n"] == n for q in trace) for n, _ in si.SERVE_GRIDS},
            "hbm_budget_gb": hbm_budget / 1e9, "slots_per_bucket": slots}
     runs = {}
-    for name, fn in (("plain_fp64", plain), ("served_mixed", lambda: served(1)), ("served_fp64", lambda: served(0))):
+    for name, fn in (("plain_fp64", plain), ("served_hybrid", lambda: served(2)), ("served_mixed", lambda: served(1)),
+                     ("served_fp64", lambda: served(0))):
         if name in arms:
             out[name], rs, service = fn()
             runs[name] = (rs, service)
@@ -680,7 +702,7 @@ def kernel_case(args):
     from paper_2602_17950_gb300.build import build
     build()
     n = (args.kernel_case, args.kernel_case)
-    prec = 1 if args.precision == "mixed" else 0
+    prec = {"fp64": 0, "mixed": 1, "hybrid": 2}[args.precision]
     psi = np.stack([si.gaussian_guess(n, L_BOX, si.seed_for(2, k), vortex=True) for k in range(args.batch)])
     with Problem(n, L_BOX, [PAR] * args.batch) as p:
         p.set_initial(psi)
@@ -690,8 +712,8 @@ def kernel_case(args):
     out = {"kernel_case": f"{n[0]}x{n[1]} x {args.batch} solves", "precision": args.precision,
            "us_per_launch": {k: round(v * 1e3, 2) for k, v in prof},
            "iteration_us": round(sum(v for _, v in prof) * 1e3, 2),
-           "gbs_per_launch": {k: round(kernel_bytes(k, n, elem) * args.batch / (v * 1e-3) / 1e9, 1)
-                              for k, v in prof if kernel_bytes(k, n, elem) > 0}}
+           "gbs_per_launch": {k: round(launch_bytes(k, n, prec) * args.batch / (v * 1e-3) / 1e9, 1)
+                              for k, v in prof if launch_bytes(k, n, prec) > 0}}
     torch.cuda.synchronize()
     print(json.dumps(out))
 
@@ -707,7 +729,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "hybrid"], default="hybrid")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed solves of the plain FP64 comparison")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -725,8 +747,8 @@ def main():
                     help="requests of the served-trace sample in the default run (0 = none)")
     ap.add_argument("--hbm-budget", type=float, default=120e9, help="device bytes the server may use")
     ap.add_argument("--slots", type=int, default=16, help="solves per server bucket")
-    ap.add_argument("--arms", default="served_mixed,served_fp64,plain_fp64", help="arms of --serve-case")
-    ap.add_argument("--sample-arms", default="plain_fp64,served_mixed", help="arms of the default run's served sample")
+    ap.add_argument("--arms", default="served_hybrid,served_fp64,plain_fp64", help="arms of --serve-case")
+    ap.add_argument("--sample-arms", default="plain_fp64,served_hybrid", help="arms of the default run's served sample")
     ap.add_argument("--case1", action="store_true", help="the small 64^2 plain-PCG workload vs the oracle")
     ap.add_argument("--case3d", action="store_true", help="the 3D mixed-precision workload (128^3)")
     ap.add_argument("--n3d", type=int, default=128, help="grid points per axis of --case3d")

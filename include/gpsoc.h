@@ -51,7 +51,15 @@ typedef enum {
 } gpsoc_status;
 
 enum { GPSOC_TRAP_HARMONIC = 0, GPSOC_TRAP_HARMONIC_QUARTIC = 1, GPSOC_TRAP_USER = 2 };
-enum { GPSOC_FP64 = 0, GPSOC_MIXED = 1 };
+/* Precision of a solve.  FP64: every array and operation in FP64.  MIXED: an FP32
+ * phase per level (FP32 arrays, FP64 sums and step decisions) until the FP32
+ * rounding floor, then FP64 iterations to the stopping rule.  HYBRID: after an
+ * FP64 lead-in (hybrid_lead_res), FP64 wave function, residual, reductions and
+ * step decisions, with H_lin Phi advanced by linearity from an FP32 H_lin P and
+ * recomputed in FP64 every hybrid_refresh iterations and before a residual is
+ * accepted; the preconditioner's and the search direction's transforms run in
+ * FP32.  HYBRID stops on the same FP64 rule as FP64 and reaches its fixed point. */
+enum { GPSOC_FP64 = 0, GPSOC_MIXED = 1, GPSOC_HYBRID = 2 };
 enum { GPSOC_STOP_DPHI = 1, GPSOC_STOP_RES = 2, GPSOC_STOP_ENERGY = 3 };
 /* Preconditioner of the PCG (Section 3.4): the combined P_C = P_V^(1/2) P_Delta P_V^(1/2)
  * (Eq. PreCondMix), the kinetic P_Delta alone (Eq. PreCondKin), the potential P_V alone
@@ -85,8 +93,7 @@ typedef struct {
 } gpsoc_params;
 
 /* Solver options.
- *   precision    GPSOC_FP64 or GPSOC_MIXED (FP32 transforms and pointwise work
- *                with FP64 reductions, then FP64 polishing to tol).
+ *   precision    GPSOC_FP64, GPSOC_MIXED or GPSOC_HYBRID (see above).
  *   stop         stopping criterion (Section 3.4, Eqs. stop1-stop3).
  *   tol          tolerance of that criterion.
  *   res_tol      if > 0, additionally require max_l ||r_l||_inf < res_tol.
@@ -114,7 +121,14 @@ typedef struct {
  *                beta = 0; 1 continues it from the FP32 phase's last direction
  *                (beta, r_prev, P_prev carried over; measured slower on the 512^2
  *                workload, so off by default).  A solve that took no FP32 step on a
- *                level keeps its FP64 state unchanged. */
+ *                level keeps its FP64 state unchanged.
+ *   hybrid_refresh GPSOC_HYBRID only: iterations between exact FP64
+ *                recomputations of H_lin Phi (0 = 16).
+ *   hybrid_lead_res GPSOC_HYBRID only: the first (coarsest) level first runs
+ *                FP64 iterations until max_l ||r_l||_inf < hybrid_lead_res (the early
+ *                iterations from the initial guess decide which local minimum is
+ *                reached), then the hybrid ones; finer levels are hybrid throughout.
+ *                0 selects 1e-4, a negative value runs no FP64 lead-in. */
 typedef struct {
   int precision;
   int stop;
@@ -130,6 +144,8 @@ typedef struct {
   int precond;
   double fp32_res_switch;
   int fp32_carry;
+  int hybrid_refresh;
+  double hybrid_lead_res;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;

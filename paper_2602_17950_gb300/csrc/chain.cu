@@ -138,7 +138,7 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
   C* buf0 = s_tw + fft_padded_len<C>(nx);
   const int per = R * nx;             // elements of one component in the tile
   const int NP = fft_padded_len<C>(nx), CP = R * NP;   // padded line length, component stride in smem
-  constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN);
+  constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN || MODE == ROW_INV_P_HY);
   C* buf1 = buf0 + 3 * CP;
   double* red = (double*)(buf1 + (two ? 3 * CP : 0));
   load_tw<T>(s_tw, A.tw[0], nx, ept);
@@ -149,7 +149,8 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
   const PhysDev ph = A.phys[s];
   const int ny = A.g.n[1];
 
-  if (MODE == ROW_FWD_PLAIN || MODE == ROW_FWD_UPD || MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE) {
+  if (MODE == ROW_FWD_PLAIN || MODE == ROW_FWD_UPD || MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE ||
+      MODE == ROW_FWD_PRE_HY) {
     W acc[1] = {(W)0};
     const W cproj = pick<W>(S.cproj, S.fcproj), mu = A.given_r ? (W)0 : pick<W>(S.mu, S.fmu), beta = pick<W>(S.beta, S.fbeta);
     const bool use_prev = (MODE == ROW_FWD_PROJ) && pick<W>(S.beta, S.fbeta) != (W)0;
@@ -195,6 +196,47 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
           acc[0] += p.x * p.x + p.y * p.y;
           buf0[c * CP + pos] = p;
         }
+      } else if (MODE == ROW_FWD_PRE_HY) {
+        // GPSOC_HYBRID: H Phi = H_lin Phi + c0 rho Phi + c1 (F.f) Phi and r = H Phi - mu Phi in
+        // FP64 from the FP64 state (the residual keeps FP64 accuracy), stored as FP32; the
+        // preconditioner's transforms then run on P_V^{1/2} r in FP32
+        const int pk = A.sc.opts.precond;
+        const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
+        double2 f[3], hl[3];
+        double m[3], rho = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          f[c] = A.phi64[sbase + c * npts + off];
+          hl[c] = A.hl64[sbase + c * npts + off];
+          m[c] = f[c].x * f[c].x + f[c].y * f[c].y;
+          rho += m[c];
+        }
+        double ax, ay;
+        spin_a<double>(f[0], f[1], f[2], ax, ay);
+        const double Fz = m[0] - m[2];
+        double fr[3], fi[3];
+        fr[0] = Fz * f[0].x + (ax * f[1].x - ay * f[1].y);
+        fi[0] = Fz * f[0].y + (ax * f[1].y + ay * f[1].x);
+        fr[1] = (ax * f[0].x + ay * f[0].y) + (ax * f[2].x - ay * f[2].y);
+        fi[1] = (ax * f[0].y - ay * f[0].x) + (ax * f[2].y + ay * f[2].x);
+        fr[2] = (ax * f[1].x + ay * f[1].y) - Fz * f[2].x;
+        fi[2] = (ax * f[1].y - ay * f[1].x) - Fz * f[2].y;
+        const double mu64 = S.mu, c0d = ph.c0, c1d = ph.c1;
+        const long long row = off / nx;
+        const W V = trap_value<W>(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
+        const W rhow = (W)rho;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double rr = hl[c].x + c0d * rho * f[c].x + c1d * fr[c] - mu64 * f[c].x;
+          const double ri = hl[c].y + c0d * rho * f[c].y + c1d * fi[c] - mu64 * f[c].y;
+          const C rc = mk<C>(rr, ri);
+          A.out1[sbase + c * npts + off] = rc;
+          acc[0] = fmax(acc[0], (W)sqrt((W)(rr * rr + ri * ri)));
+          W den = al[c] + V + c0 * rhow;
+          den = fmax(den, (W)1e-12 * al[c]);
+          const W sc = use_pv ? rsqrt_w<W>(den) : (W)1;
+          buf0[c * CP + pos] = mk<C>(rc.x * sc, rc.y * sc);
+        }
       } else {  // ROW_FWD_PRE: r = H Phi - mu Phi, then P_V^{1/2} r (Eq. PreCondPot)
         const int pk = A.sc.opts.precond;
         const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
@@ -229,12 +271,14 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.out0[sbase + c * npts + rbase + e] = buf0[c * CP + pos];
     }
-    if (MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE || (MODE == ROW_FWD_UPD && upd)) {
+    if (MODE == ROW_FWD_PROJ || MODE == ROW_FWD_PRE || MODE == ROW_FWD_PRE_HY || (MODE == ROW_FWD_UPD && upd)) {
       const bool mx[1] = {MODE != ROW_FWD_PROJ};
-      const int slots[1] = {(MODE == ROW_FWD_PROJ) ? (int)SL_P2 : (MODE == ROW_FWD_PRE) ? (int)SL_RINF : (int)SL_DPHIINF};
+      const int slots[1] = {(MODE == ROW_FWD_PROJ) ? (int)SL_P2
+                            : (MODE == ROW_FWD_PRE || MODE == ROW_FWD_PRE_HY) ? (int)SL_RINF : (int)SL_DPHIINF};
       store_partials<1, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
     }
-    if (MODE == ROW_FWD_PRE && A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_res(A.sc, s, red);
+    if ((MODE == ROW_FWD_PRE || MODE == ROW_FWD_PRE_HY) && A.fuse && last_block(A.cnt, s, bps, &last_flag))
+      sc_res(A.sc, s, red);
     return;
   }
 
@@ -312,6 +356,7 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
 
   // ROW_INV_H / ROW_INV_P / ROW_INV_LIN: lin = F_x^-1(T')/npts - Omega x F_x^-1(G)/npts + V u
   const W c0 = pick<W>(ph.c0, ph.fc0), c1 = pick<W>(ph.c1, ph.fc1);
+  double rphi = 0.0, pp64 = 0.0;   // ROW_INV_P_HY: Re<P, Phi> against the FP64 Phi and ||P||^2, summed in FP64
   W acc[13];
 #pragma unroll
   for (int k = 0; k < 13; ++k) acc[k] = (W)0;
@@ -373,6 +418,18 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
       C f[3], h[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) { f[c] = A.in3[sbase + c * npts + off]; h[c] = A.in4[sbase + c * npts + off]; }
+      if constexpr (MODE == ROW_INV_P_HY) {
+        // H_lin P kept for the update of H_lin Phi by linearity; the radial part of P
+        // in FP64 (P's FP32 values against the FP64 Phi) for the exact tangent correction
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          A.out0[sbase + c * npts + off] = mk<C>(lin_r[c], lin_i[c]);
+          const double2 g = A.phi64[sbase + c * npts + off];
+          const double ux = (double)u[c].x, uy = (double)u[c].y;
+          rphi += g.x * ux + g.y * uy;
+          pp64 += ux * ux + uy * uy;
+        }
+      }
       W hpp = (W)0, hphip = (W)0, Rv = (W)0, rf = (W)0, rp = (W)0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -423,6 +480,16 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
     const int slots[13] = {SL_HPP, SL_HPHIP, SL_RPHI, SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,
                            SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP};
     store_partials<13, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
+    if constexpr (MODE == ROW_INV_P_HY) {
+      // the normalisation of the step needs these two to FP64 accuracy
+      double v2[2] = {rphi, pp64};
+      const bool mx2[2] = {false, false};
+      block_reduce<2>(v2, red, mx2);
+      if (threadIdx.x == 0) {
+        A.part[(sslot + SL_RPHI) * A.pmax + rb] = v2[0];
+        A.part[(sslot + SL_P2) * A.pmax + rb] = v2[1];
+      }
+    }
     if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_step(A.sc, s, red);
   }
 }
@@ -561,6 +628,40 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 
   // forward transform along the axis: natural-order spectrum in buf
   row_fft<C, false, 1, true>(buf, buf, 3 * TC, NPL, La, s_tw, ept);
+
+  if ((MODE == COL_YMID_H || MODE == COL_MID_H) && A.xhat) {
+    // GPSOC_HYBRID P chain: buf holds the full spectrum of P.  Advance the stored spectrum
+    // of Phi by the step applied this iteration (Phi_hat <- g (c Phi_hat + t P_hat_prev)),
+    // keep this P_hat, and sum 1/2 |k|^2 |Phi_hat_l|^2 and 1/2 |k|^2 Re(Phi_hat_l conj P_hat_l)
+    const bool upd = A.khat_upd && S.upd_applied;
+    const W uc = pick<W>(S.upd_c, S.fupd_c), us = pick<W>(S.upd_s, S.fupd_s), usc = pick<W>(S.upd_scale, S.fupd_scale);
+    W kacc[6] = {(W)0, (W)0, (W)0, (W)0, (W)0, (W)0};
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int j = e / TC, t = e - j * TC;
+      W kx, ky, kz = (W)0;
+      kinner(t, kx, ky);
+      if (axis == 1) ky = wavenum<W>(j, na, piA);
+      else kz = wavenum<W>(j, na, piA);
+      const W k2h = (W)0.5 * (kx * kx + ky * ky + kz * kz);
+      const long long gi = sbase + obase + (long long)j * ni + t;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const C pv = buf[sidx(c, t, j)];
+        C xv = A.xhat[gi + c * npts];
+        if (upd) {
+          const C po = A.phat[gi + c * npts];
+          xv = mk<C>(usc * (uc * xv.x + us * po.x), usc * (uc * xv.y + us * po.y));
+          A.xhat[gi + c * npts] = xv;
+        }
+        A.phat[gi + c * npts] = pv;
+        kacc[c] += k2h * (xv.x * xv.x + xv.y * xv.y);
+        kacc[3 + c] += k2h * (xv.x * pv.x + xv.y * pv.y);
+      }
+    }
+    const bool kmx[6] = {false, false, false, false, false, false};
+    const int kslots[6] = {SL_KPHI0, SL_KPHI1, SL_KPHI2, SL_KX0, SL_KX1, SL_KX2};
+    store_partials<6, W>(kacc, kslots, kmx, red, A.part, (long long)s * NSLOT, A.pmax, tb);
+  }
 
   if (MODE == COL_YMID_H) {
     // G_c = F_y^-1[v_y F_y A_c] for the three components at once (buf2)
@@ -738,7 +839,7 @@ static size_t row_smem(const Geo& g, int mode, int nsolve) {
   using C = cx_t<T>;
   const int R = row_rows_per_block<T>(g, nsolve);
   const int per = R * g.n[0];
-  const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN);
+  const bool two = (mode == ROW_INV_H || mode == ROW_INV_P || mode == ROW_INV_LIN || mode == ROW_INV_P_HY);
   (void)per;
   const int CP = R * fft_padded_len<C>(g.n[0]);
   return sizeof(C) * (fft_padded_len<C>(g.n[0]) + 3 * CP * (two ? 2 : 1)) + kRedDoubles * sizeof(double);
@@ -776,6 +877,8 @@ void launch_row(int mode, const ChainArgs<T>& a, int, const Launch&, cudaStream_
     case ROW_INV_PLAIN: row_go<T, ROW_INV_PLAIN>(a, st); break;
     case ROW_INV_LIN: row_go<T, ROW_INV_LIN>(a, st); break;
     case ROW_FWD_UPD: row_go<T, ROW_FWD_UPD>(a, st); break;
+    case ROW_FWD_PRE_HY: row_go<T, ROW_FWD_PRE_HY>(a, st); break;
+    case ROW_INV_P_HY: row_go<T, ROW_INV_P_HY>(a, st); break;
   }
 }
 
@@ -809,6 +912,7 @@ cudaError_t chain_prepare() {
   GPSOC_ATTR((k_row<T, ROW_FWD_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_FWD_PROJ>)) GPSOC_ATTR((k_row<T, ROW_FWD_PRE>))
   GPSOC_ATTR((k_row<T, ROW_INV_H>)) GPSOC_ATTR((k_row<T, ROW_INV_P>)) GPSOC_ATTR((k_row<T, ROW_INV_PRE>))
   GPSOC_ATTR((k_row<T, ROW_INV_PLAIN>)) GPSOC_ATTR((k_row<T, ROW_INV_LIN>)) GPSOC_ATTR((k_row<T, ROW_FWD_UPD>))
+  GPSOC_ATTR((k_row<T, ROW_FWD_PRE_HY>)) GPSOC_ATTR((k_row<T, ROW_INV_P_HY>))
   GPSOC_ATTR((k_col<T, COL_FWD>)) GPSOC_ATTR((k_col<T, COL_INV>)) GPSOC_ATTR((k_col<T, COL_MID_H>))
   GPSOC_ATTR((k_col<T, COL_MID_PRE>)) GPSOC_ATTR((k_col<T, COL_YMID_H>)) GPSOC_ATTR((k_col<T, COL_YINV_H>))
   if constexpr (sizeof(T) == 4) {

@@ -69,12 +69,13 @@ struct Bufs {
   using C = cx_t<T>;
   C *Phi = nullptr, *HPhi = nullptr, *R[2] = {nullptr, nullptr}, *P[2] = {nullptr, nullptr};
   C *Z = nullptr, *D = nullptr, *A = nullptr, *B = nullptr, *W = nullptr, *G = nullptr;
+  C *Xh = nullptr, *Ph = nullptr;   // GPSOC_HYBRID (FP32 set): spectra of Phi and of the last P
 };
 
 
 const char* row_name(int m) {
   static const char* n[] = {"row_fwd", "row_fwd_proj", "row_fwd_pre", "row_inv_h", "row_inv_p", "row_inv_pre",
-                            "row_inv_plain", "row_inv_lin", "row_fwd_upd"};
+                            "row_inv_plain", "row_inv_lin", "row_fwd_upd", "row_fwd_pre_hy", "row_inv_p_hy"};
   return (m >= 0 && m < (int)(sizeof(n) / sizeof(n[0]))) ? n[m] : "row_?";
 }
 const char* col_name(int m, int axis) {
@@ -120,10 +121,11 @@ struct gpsoc_problem {
   bool has_state = false;
   int max_level = 0;
   // captured iteration graph (two iterations) for the current level / options
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0] FP64, [1] FP32 iteration graphs
-  int graph_level[2] = {-1, -1};
-  OptsDev graph_opts[2]{};
-  uint64_t graph_kernels[2] = {0, 0};   // kernels per replay of the captured graph
+  // [0] FP64, [1] FP32, [2] hybrid, [3] hybrid opening with the exact FP64 recomputation
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_level[4] = {-1, -1, -1, -1};
+  OptsDev graph_opts[4]{};
+  uint64_t graph_kernels[4] = {0, 0, 0, 0};   // kernels per replay of the captured graph
   uint64_t launches = 0;        // kernels launched so far (graph replays included)
   Tracker* tr = nullptr;        // active tracker while enqueueing
   std::vector<std::string> prof_names;
@@ -528,7 +530,7 @@ gpsoc_status ensure_fp32(gpsoc_problem* p) {
   const Geo g = make_geo(p, 0);
   const size_t arr = sizeof(float2) * (size_t)p->batch * 3 * g.npts;
   float2** slots[] = {&p->b32.Phi, &p->b32.HPhi, &p->b32.R[0], &p->b32.R[1], &p->b32.P[0], &p->b32.P[1],
-                      &p->b32.Z, &p->b32.D, &p->b32.A, &p->b32.B, &p->b32.W, &p->b32.G};
+                      &p->b32.Z, &p->b32.D, &p->b32.A, &p->b32.B, &p->b32.W, &p->b32.G, &p->b32.Xh, &p->b32.Ph};
   for (float2** sl : slots) {
     if (cudaMalloc(sl, arr) != cudaSuccess) { cudaGetLastError(); return fail(GPSOC_ENOMEM, "device allocation failed (FP32 set)"); }
   }
@@ -546,13 +548,271 @@ gpsoc_status convert_state(gpsoc_problem* p, int level, bool to32) {
   return GPSOC_OK;
 }
 
+// ==================================================================== GPSOC_HYBRID
+// The wave function, H_lin Phi, the residual r = H(Phi) - mu Phi, every reduction of
+// the state and Algorithm 2 stay FP64; the preconditioner's and the direction's
+// transforms (and H_lin P) run in FP32.  H_lin Phi^{n+1} is formed from H_lin Phi^n and
+// H_lin P^n by linearity (the step is a linear combination of Phi^n and P^n), and
+// recomputed exactly in FP64 every few iterations and before a solve's residual is
+// accepted, so the fixed point is the FP64 one: only the search directions carry FP32
+// rounding.
+
+HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, int parity, int gate, int flags) {
+  HyArgs h{};
+  h.st = p->d_st;
+  h.phys = p->d_phys;
+  h.part = p->d_part;
+  h.pmax = p->pmax;
+  h.g = g;
+  h.trap = make_trap(p, level);
+  h.phi = p->b64.Phi;
+  h.hl = p->b64.HPhi;
+  h.p = p->b32.P[(parity & 1) ^ 1];   // direction of the previous iteration
+  h.hlp = p->b32.HPhi;                // its H_lin P
+  h.phi32 = p->b32.Phi;
+  h.npts = g.npts;
+  h.bps = row_blocks_per_solve<double>(g, p->batch);
+  h.nsolve = p->batch;
+  h.gate = gate;
+  h.flags = flags;
+  h.fuse = (flags & HY_REDUCE) ? 1 : 0;
+  h.cnt = p->d_cnt;
+  h.sc = sc;
+  return h;
+}
+
+void HY(gpsoc_problem* p, const HyArgs& h) {
+  launch_hy_upd(h, p->stream);
+  mark(p, (h.flags & HY_REDUCE) ? "hy_upd" : "hy_step");
+}
+
+// exact FP64 H_lin Phi into b64.HPhi and the per-component kinetic sums into the state
+gpsoc_status hy_exact_hlin(gpsoc_problem* p, int level, int gate) {
+  ChainArgs<double> d;
+  gpsoc_status s = chain_args<double>(p, level, d);
+  if (s != GPSOC_OK) return s;
+  Bufs<double>& D = p->b64;
+  d.gate = gate;
+  d.fuse = 0;
+  d.in0 = D.Phi; d.out0 = D.A;
+  RL<double>(p, ROW_FWD_PLAIN, d);
+  h_middle<double>(p, d, D);
+  ChainArgs<double> l = d;
+  l.in0 = D.W; l.in1 = D.G; l.in2 = D.Phi; l.out0 = D.HPhi; l.out1 = nullptr;
+  RL<double>(p, ROW_INV_LIN, l);
+  ScalarArgs x = scalar_args<double>(p, level, PH_KIN, d.g);
+  x.force = (gate == GATE_ALL) ? 1 : 0;
+  SL(p, x);
+  return GPSOC_OK;
+}
+
+// One GPSOC_HYBRID iteration for every active solve; `exact` opens it with the exact
+// FP64 recomputation of H_lin Phi instead of the update by linearity.
+gpsoc_status enqueue_iteration_hy(gpsoc_problem* p, int level, int parity, const OptsDev& o, bool exact) {
+  ChainArgs<float> a;
+  gpsoc_status s = chain_args<float>(p, level, a);
+  if (s != GPSOC_OK) return s;
+  const Geo g = a.g;
+  const int cur = parity & 1, prv = cur ^ 1;
+  a.sc = scalar_ctx<float>(p, g, o, 2 | (cur << 2) | 8);
+  Bufs<float>& F = p->b32;
+  Bufs<double>& D = p->b64;
+  // apply the pending step; H_lin Phi by linearity or exactly; E, mu, alpha, masses (FP64)
+  if (exact) {
+    HY(p, hy_args(p, level, g, a.sc, parity, GATE_ACTIVE, HY_UPD));
+    s = hy_exact_hlin(p, level, GATE_ACTIVE);
+    if (s != GPSOC_OK) return s;
+    HY(p, hy_args(p, level, g, a.sc, parity, GATE_ACTIVE, HY_REDUCE));
+    // the spectrum of Phi, from its FP32 copy, for the kinetic sums of the P chain
+    ChainArgs<float> t = a;
+    t.fuse = 0;
+    t.in0 = F.Phi; t.out0 = F.B;
+    RL<float>(p, ROW_FWD_PLAIN, t);
+    t.in0 = F.B; t.out0 = (p->dim == 2) ? F.Xh : F.B;
+    CL<float>(p, COL_FWD, 1, t);
+    if (p->dim == 3) {
+      t.in0 = F.B; t.out0 = F.Xh;
+      CL<float>(p, COL_FWD, 2, t);
+    }
+  } else {
+    HY(p, hy_args(p, level, g, a.sc, parity, GATE_ACTIVE, HY_UPD | HY_REC | HY_REDUCE));
+  }
+  // r in FP64 (stored FP32), stopping test, P_C r in FP32, beta
+  ChainArgs<float> f = a;
+  f.fuse = 1;
+  f.phi64 = D.Phi; f.hl64 = D.HPhi; f.out0 = F.A; f.out1 = F.R[cur];
+  RL<float>(p, ROW_FWD_PRE_HY, f);
+  ChainArgs<float> m = a;
+  m.fuse = 0;
+  m.in0 = F.A; m.out0 = F.A;
+  if (p->dim == 2) {
+    CL<float>(p, COL_MID_PRE, 1, m);
+  } else {
+    CL<float>(p, COL_FWD, 1, m);
+    CL<float>(p, COL_MID_PRE, 2, m);
+    m.scale = 1.0;
+    CL<float>(p, COL_INV, 1, m);
+  }
+  ChainArgs<float> iv = a;
+  iv.fuse = 1;
+  iv.in0 = F.A; iv.in1 = F.Phi; iv.in2 = F.R[cur]; iv.in3 = F.R[prv]; iv.out0 = F.Z;
+  RL<float>(p, ROW_INV_PRE, iv);
+  // Re<D, Phi>, the slope Re<r, D> and the beta = 0 decision
+  ElemArgs<float> e = elem_args<float>(p, g, GATE_ACTIVE);
+  e.in0 = F.Z; e.in1 = F.P[prv]; e.in2 = F.Phi; e.in3 = F.R[cur];
+  e.fuse = 1;
+  e.cnt = p->d_cnt;
+  e.sc = a.sc;
+  EL<float>(p, EL_DIR, e);
+  // P, H_lin P (kept), step model with Re<r, P> and the FP64 radial part, Algorithm 2
+  ChainArgs<float> pf = a;
+  pf.fuse = 0;
+  pf.in0 = F.Z; pf.in1 = F.Phi; pf.in2 = F.P[prv]; pf.out0 = F.A; pf.out1 = F.P[cur];
+  RL<float>(p, ROW_FWD_PROJ, pf);
+  ChainArgs<float> pm = a;
+  pm.xhat = F.Xh; pm.phat = F.Ph; pm.khat_upd = exact ? 0 : 1;
+  h_middle<float>(p, pm, F);
+  ChainArgs<float> pi = a;
+  pi.fuse = 1;
+  pi.in0 = F.W; pi.in1 = F.G; pi.in2 = F.P[cur]; pi.in3 = F.Phi; pi.in4 = F.R[cur];
+  pi.phi64 = D.Phi; pi.out0 = F.HPhi; pi.out1 = nullptr;
+  RL<float>(p, ROW_INV_P_HY, pi);
+  CK(cudaGetLastError());
+  return GPSOC_OK;
+}
+
+gpsoc_status build_graph_hy(gpsoc_problem* p, int level, const OptsDev& o, bool exact) {
+  const int k = exact ? 3 : 2;
+  if (p->graph[k] && p->graph_level[k] == level && std::memcmp(&p->graph_opts[k], &o, sizeof(o)) == 0) return GPSOC_OK;
+  if (p->graph[k]) { cudaGraphExecDestroy(p->graph[k]); p->graph[k] = nullptr; }
+  cudaGraph_t gr;
+  Tracker tr;
+  tr.stream = p->stream;
+  CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  p->tr = &tr;
+  gpsoc_status s = enqueue_iteration_hy(p, level, 0, o, exact);
+  if (s == GPSOC_OK) s = enqueue_iteration_hy(p, level, 1, o, false);
+  cudaError_t e = cudaStreamEndCapture(p->stream, &gr);
+  p->tr = nullptr;
+  p->graph_kernels[k] = tr.count;
+  if (s != GPSOC_OK) { if (e == cudaSuccess) cudaGraphDestroy(gr); return s; }
+  if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p->graph[k], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return fail(GPSOC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  p->graph_level[k] = level;
+  p->graph_opts[k] = o;
+  return GPSOC_OK;
+}
+
+// The stopping rule with the exact residual: for every solve that has stopped with
+// status OK, recompute H_lin Phi in FP64, then E, mu, alpha and the residual; a solve
+// whose exact residual misses the rule continues (*resumed counts them).  Buffer
+// parity 0 is used, the parity the next iteration graph starts with.
+gpsoc_status hy_verify(gpsoc_problem* p, int level, const OptsDev& o, int* resumed) {
+  *resumed = 0;
+  const Geo g = make_geo(p, level);
+  OptsDev ov = o;
+  ov.no_stop = 1;
+  const ScalarCtx sc = scalar_ctx<float>(p, g, ov, 2 | 8);
+  HY(p, hy_args(p, level, g, sc, 0, GATE_ALL, HY_UPD));
+  gpsoc_status s = hy_exact_hlin(p, level, GATE_ALL);
+  if (s != GPSOC_OK) return s;
+  HY(p, hy_args(p, level, g, sc, 0, GATE_ALL, HY_REDUCE));
+  ChainArgs<float> f;
+  s = chain_args<float>(p, level, f);
+  if (s != GPSOC_OK) return s;
+  f.gate = GATE_ALL;
+  f.sc = sc;
+  f.fuse = 1;
+  f.phi64 = p->b64.Phi; f.hl64 = p->b64.HPhi; f.out0 = p->b32.A; f.out1 = p->b32.R[0];
+  RL<float>(p, ROW_FWD_PRE_HY, f);
+  CK(cudaGetLastError());
+  s = sync_state(p);
+  if (s != GPSOC_OK) return s;
+  for (int i = 0; i < p->batch; ++i) {
+    SolveState& S = p->h_st[i];
+    if (S.active || S.status != GPSOC_OK) continue;
+    bool ok = true;
+    if (o.stop == GPSOC_STOP_RES) ok = S.res_inf < o.tol;
+    if (o.res_tol > 0.0) ok = ok && S.res_inf < o.res_tol;
+    // resume with beta = 0: the check's residual took the buffer of one stored direction
+    if (!ok) { S.active = 1; S.first = 1; ++*resumed; }
+  }
+  if (*resumed) {
+    CK(cudaMemcpyAsync(p->d_st, p->h_st, sizeof(SolveState) * p->batch, cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  return GPSOC_OK;
+}
+
+int hy_refresh_every(const gpsoc_opts* o) { return o->hybrid_refresh > 0 ? o->hybrid_refresh : 16; }
+double hy_lead_res(const gpsoc_opts* o) {
+  return o->hybrid_lead_res > 0 ? o->hybrid_lead_res : (o->hybrid_lead_res < 0 ? 0.0 : 1e-4);
+}
+
+// options of an FP64 lead-in phase: the solve's own stopping rule, and the phase also ends
+// (without ending the solve) once max|r| < lead_res, on stagnation or at the iteration cap
+OptsDev lead_opts(const OptsDev& o, double lead_res) {
+  OptsDev l = o;
+  l.phase32 = 1;
+  l.res32 = lead_res;
+  l.tol_rel = 0.0;
+  return l;
+}
+
+// replay the hybrid graphs until every solve has stopped with its exact residual
+gpsoc_status iterate_until_done_hy(gpsoc_problem* p, int level, const OptsDev& o, int check_every, int refresh) {
+  gpsoc_status s = build_graph_hy(p, level, o, false);
+  if (s == GPSOC_OK) s = build_graph_hy(p, level, o, true);
+  if (s != GPSOC_OK) return s;
+  const int pairs = (check_every + 1) / 2;
+  const int every = std::max(1, refresh / 2);   // pairs between exact recomputations
+  for (int round = 0; round < 8; ++round) {
+    long long k = 0;
+    const long long cap = (long long)o.max_iter + 4;
+    for (long long it = 0; it <= cap; it += 2 * pairs) {
+      for (int r = 0; r < pairs; ++r, ++k) {
+        const int gk = (k % every == 0) ? 3 : 2;
+        CK(cudaGraphLaunch(p->graph[gk], p->stream));
+        p->launches += p->graph_kernels[gk];
+      }
+      s = sync_state(p);
+      if (s != GPSOC_OK) return s;
+      bool any = false;
+      for (int i = 0; i < p->batch; ++i) any |= (p->h_st[i].active != 0);
+      if (!any) break;
+    }
+    int resumed = 0;
+    s = hy_verify(p, level, o, &resumed);
+    if (s != GPSOC_OK || resumed == 0) return s;
+  }
+  return GPSOC_OK;
+}
+
 // One multigrid level.  FP64: PCG to the stopping rule.  MIXED: PCG in FP32
 // arrays (FP64 reductions and scalars) until the energy change falls below
 // fp32_rel * |E| or Algorithm 2 finds no decrease (the FP32 rounding floor),
 // then PCG in FP64 from that iterate (beta restarted) to the stopping rule.
 gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level,
-                       int precision, double fp32_rel, bool carry) {
+                       int precision, double fp32_rel, bool carry, int refresh, double lead_res) {
   gpsoc_status s;
+  if (precision == GPSOC_HYBRID) {
+    s = ensure_fp32(p);
+    if (s != GPSOC_OK) return s;
+    s = init_level(p, level, first_level);
+    if (s != GPSOC_OK) return s;
+    if (lead_res > 0.0 && first_level) {
+      // FP64 iterations until max|r| < lead_res on the first level (the early iterations
+      // from the initial guess decide which local minimum the solve reaches; finer levels
+      // start from the prolonged solution of that minimum)
+      s = iterate_until_done<double>(p, level, lead_opts(o, lead_res), check_every);
+      if (s != GPSOC_OK) return s;
+      s = init_level(p, level, false);
+      if (s != GPSOC_OK) return s;
+    }
+    return iterate_until_done_hy(p, level, o, check_every, refresh);
+  }
   if (precision == GPSOC_MIXED) {
     s = ensure_fp32(p);
     if (s != GPSOC_OK) return s;
@@ -598,6 +858,7 @@ long long mixed_min_points(const gpsoc_opts* opts) {
 }
 
 int level_precision(const gpsoc_problem* p, int level, const gpsoc_opts* opts) {
+  if (opts->precision == GPSOC_HYBRID) return GPSOC_HYBRID;
   if (opts->precision != GPSOC_MIXED) return GPSOC_FP64;
   const Geo g = make_geo(p, level);
   return (long long)p->batch * g.npts >= mixed_min_points(opts) ? GPSOC_MIXED : GPSOC_FP64;
@@ -910,12 +1171,12 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
 void gpsoc_destroy(gpsoc_problem* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  for (int k = 0; k < 2; ++k) if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
+  for (int k = 0; k < 4; ++k) if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
   double2* arrs[] = {p->b64.Phi, p->b64.HPhi, p->b64.R[0], p->b64.R[1], p->b64.P[0], p->b64.P[1],
                      p->b64.Z, p->b64.D, p->b64.A, p->b64.B, p->b64.W, p->b64.G};
   for (double2* a : arrs) if (a) cudaFree(a);
   float2* arrs32[] = {p->b32.Phi, p->b32.HPhi, p->b32.R[0], p->b32.R[1], p->b32.P[0], p->b32.P[1],
-                      p->b32.Z, p->b32.D, p->b32.A, p->b32.B, p->b32.W, p->b32.G};
+                      p->b32.Z, p->b32.D, p->b32.A, p->b32.B, p->b32.W, p->b32.G, p->b32.Xh, p->b32.Ph};
   for (float2* a : arrs32) if (a) cudaFree(a);
   for (auto& kv : p->tw64) cudaFree(kv.second);
   for (auto& kv : p->tw32) cudaFree(kv.second);
@@ -1004,7 +1265,8 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!opts) return fail(GPSOC_EINVAL, "opts is NULL");
   if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
-  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
+  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED && opts->precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
   if (opts->stop < 0 || opts->stop > 3) return fail(GPSOC_EINVAL, "unknown stopping criterion");
   if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   if (!(opts->tol > 0)) return fail(GPSOC_EINVAL, "tol must be > 0");
@@ -1026,7 +1288,7 @@ gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result*
     }
     const int lp = level_precision(p, lev, opts);
     s = run_level(p, lev, o, check, lev == levels - 1, lp, opts->fp32_switch > 0 ? opts->fp32_switch : 1e-10,
-                  opts->fp32_carry != 0);
+                  opts->fp32_carry != 0, hy_refresh_every(opts), hy_lead_res(opts));
     if (lp != GPSOC_MIXED)
       for (int i = 0; i < p->batch; ++i) p->level_res32[i].push_back(0.0);
     if (s != GPSOC_OK) return s;
@@ -1053,6 +1315,36 @@ gpsoc_status gpsoc_iterate(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   if (!opts || iters < 0) return fail(GPSOC_EINVAL, "bad arguments");
   if (opts->precond < 0 || opts->precond > 3) return fail(GPSOC_EINVAL, "unknown preconditioner");
   if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  if (opts->precision == GPSOC_HYBRID) {
+    // exact FP64 H_lin Phi on the first iteration and every hybrid_refresh iterations
+    OptsDev o = make_opts(opts);
+    o.no_stop = 1;
+    gpsoc_status s = ensure_fp32(p);
+    if (s != GPSOC_OK) return s;
+    if (restart) {
+      s = init_level(p, p->level, true);
+      if (s != GPSOC_OK) return s;
+    }
+    const int every = hy_refresh_every(opts);
+    for (int k = 0; k < iters; ++k) {
+      s = enqueue_iteration_hy(p, p->level, k & 1, o, k % every == 0);
+      if (s != GPSOC_OK) return s;
+    }
+    if (iters > 0) {
+      const Geo g = make_geo(p, p->level);
+      HY(p, hy_args(p, p->level, g, scalar_ctx<float>(p, g, o, 2 | 8), iters & 1, GATE_PENDING, HY_UPD));
+      ScalarArgs x = scalar_args<float>(p, p->level, PH_CLEAR, g);
+      SL(p, x);
+      CK(cudaGetLastError());
+    }
+    s = sync_state(p);
+    if (s != GPSOC_OK) return s;
+    p->level_iters.assign(p->batch, std::vector<int>());
+    p->level_fp32.assign(p->batch, std::vector<int>());
+    p->level_res32.assign(p->batch, std::vector<double>());
+    if (results) fill_results(p, results, 1);
+    return GPSOC_OK;
+  }
   if (check_precision(opts->precision) != GPSOC_OK) return GPSOC_EINVAL;
   OptsDev o = make_opts(opts);
   o.no_stop = 1;
@@ -1178,19 +1470,23 @@ gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   size_t per = 0;
   std::vector<size_t> starts;
   const bool f32 = (opts->precision == GPSOC_MIXED);
-  if (f32) {
+  const bool hy = (opts->precision == GPSOC_HYBRID);
+  if (f32 || hy) {
     p->tr = nullptr;
     s = ensure_fp32(p);
-    if (s == GPSOC_OK) s = convert_state(p, p->level, true);
+    if (s == GPSOC_OK && f32) s = convert_state(p, p->level, true);
+    // hybrid: an untimed opening iteration with the exact H_lin Phi, then the timed ones
+    if (s == GPSOC_OK && hy) s = enqueue_iteration_hy(p, p->level, 0, o, true);
     p->tr = &tr;
   }
   for (int k = 0; k < iters && s == GPSOC_OK; ++k) {
     starts.push_back(tr.evs.size());
     tr.start();
-    if (f32) s = enqueue_iteration<float>(p, p->level, p->b32, k & 1, o, 1);
+    if (hy) s = enqueue_iteration_hy(p, p->level, (k + 1) & 1, o, false);
+    else if (f32) s = enqueue_iteration<float>(p, p->level, p->b32, k & 1, o, 1);
     else s = enqueue_iteration<double>(p, p->level, p->b64, k & 1, o, 0);
   }
-  const int last_par = (iters - 1) & 1;
+  const int last_par = hy ? (iters & 1) : ((iters - 1) & 1);
   p->tr = nullptr;
   p->launches += tr.count;
   if (s == GPSOC_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) s = fail(GPSOC_ECUDA, "profile sync failed");
@@ -1210,8 +1506,16 @@ gpsoc_status gpsoc_profile(gpsoc_problem* p, const gpsoc_opts* opts, int iters, 
   }
   for (cudaEvent_t e : tr.evs) cudaEventDestroy(e);
   if (s == GPSOC_OK) {
-    s = f32 ? flush_pending<float>(p, p->level, p->b32, last_par) : flush_pending<double>(p, p->level, p->b64, last_par);
-    if (s == GPSOC_OK && f32) s = convert_state(p, p->level, false);
+    if (hy) {
+      const Geo g = make_geo(p, p->level);
+      HY(p, hy_args(p, p->level, g, scalar_ctx<float>(p, g, o, 2 | 8), last_par ^ 1, GATE_PENDING, HY_UPD));
+      ScalarArgs x = scalar_args<float>(p, p->level, PH_CLEAR, g);
+      SL(p, x);
+      CK(cudaGetLastError());
+    } else {
+      s = f32 ? flush_pending<float>(p, p->level, p->b32, last_par) : flush_pending<double>(p, p->level, p->b64, last_par);
+      if (s == GPSOC_OK && f32) s = convert_state(p, p->level, false);
+    }
   }
   return s;
 }
@@ -1295,6 +1599,9 @@ struct Bucket {
   cudaEvent_t done = nullptr;  // recorded after the last launched round of iterations
   bool in_flight = false;
   uint64_t launched = 0;       // launch sequence number of the round in flight
+  bool hybrid = false;         // GPSOC_HYBRID graphs (FP64 state, FP32 directions)
+  bool fp32_phase = false;     // GPSOC_MIXED first stage: FP32 arrays
+  int refresh = 16;            // hybrid: iterations between exact recomputations of H_lin Phi
 };
 
 bool bucket_empty(const Bucket* b) {
@@ -1341,7 +1648,7 @@ namespace {
 size_t bucket_bytes(const gpsoc_grid& g, int slots, int stage) {
   const size_t per = sizeof(double2) * 3 * solve_points(g);
   size_t b = 12 * per * (size_t)slots;                     // FP64 working set
-  if (stage == 1) b += 12 * (per / 2) * (size_t)slots;     // FP32 working set
+  if (stage == 1) b += 14 * (per / 2) * (size_t)slots;     // FP32 working set (FP32 phase or hybrid)
   return b + (4u << 20);
 }
 
@@ -1365,7 +1672,7 @@ gpsoc_status load_slot(Bucket* b, int s, const ServerReq& r) {
   in.only = s;
   in.flags = 1;
   SL(p, in);
-  if (b->stage == 1) {
+  if (b->fp32_phase) {
     launch_convert<float>(p->b64.Phi + off, 0, p->b32.Phi + off, (long long)3 * g.npts, p->stream);
     mark(p, "convert");
   }
@@ -1379,7 +1686,7 @@ gpsoc_status read_slot(Bucket* b, int s, ServerReq& r) {
   gpsoc_problem* p = b->p;
   const Geo g = make_geo(p, 0);
   const size_t off = (size_t)s * 3 * g.npts;
-  if (b->stage == 1) {
+  if (b->fp32_phase) {
     launch_convert<double>(p->b32.Phi + off, 1, p->b64.Phi + off, (long long)3 * g.npts, p->stream);
     mark(p, "convert");
     CK(cudaGetLastError());
@@ -1397,7 +1704,9 @@ Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_sta
       if (t < 0) return b;
   }
   const int slots = sv->opts.slots_per_bucket > 0 ? sv->opts.slots_per_bucket : 32;
-  const size_t need = bucket_bytes(r.grid, slots, stage);
+  // FP32 working set: the hybrid stage of GPSOC_HYBRID, the FP32 phase of GPSOC_MIXED
+  const bool with32 = (sv->opts.precision == GPSOC_HYBRID) ? (stage == 2) : (stage == 1);
+  const size_t need = bucket_bytes(r.grid, slots, with32 ? 1 : 2);
   // release idle empty buckets while the budget is short
   for (size_t i = 0; i < sv->buckets.size() && sv->bytes + need > (size_t)sv->opts.hbm_budget_bytes;) {
     Bucket* b = sv->buckets[i];
@@ -1414,7 +1723,12 @@ Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_sta
   std::vector<gpsoc_params> pars(slots, r.par);
   gpsoc_status s = gpsoc_create(&r.grid, &r.trap, pars.data(), slots, nullptr, &b->p);
   if (s != GPSOC_OK) { delete b; *err = s; return nullptr; }
-  if (stage == 1 && ensure_fp32(b->p) != GPSOC_OK) { bucket_free(b); *err = GPSOC_ENOMEM; return nullptr; }
+  // GPSOC_MIXED: stage 1 = FP32 phase; GPSOC_HYBRID: stage 1 = FP64 lead-in, stage 2 = hybrid
+  const bool hy_server = (sv->opts.precision == GPSOC_HYBRID);
+  b->hybrid = hy_server && stage == 2;
+  b->fp32_phase = !hy_server && stage == 1;
+  if ((b->fp32_phase || b->hybrid) && ensure_fp32(b->p) != GPSOC_OK) { bucket_free(b); *err = GPSOC_ENOMEM; return nullptr; }
+  b->refresh = hy_refresh_every(&r.opts);
   if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
     b->done = nullptr;
     bucket_free(b);
@@ -1426,11 +1740,13 @@ Bucket* find_or_make_bucket(gpsoc_server* sv, ServerReq& r, int stage, gpsoc_sta
   b->slot.assign(slots, -1);
   b->bytes = need;
   b->o = make_opts(&r.opts);
-  if (stage == 1) {
+  if (b->fp32_phase) {
     b->o.stop = GPSOC_STOP_ENERGY;
     b->o.res_tol = 0.0;
     b->o.tol_rel = r.opts.fp32_switch > 0 ? r.opts.fp32_switch : 1e-10;
     b->o.phase32 = 1;
+  } else if (hy_server && stage == 1) {
+    b->o = lead_opts(b->o, hy_lead_res(&r.opts));
   }
   // every slot starts inactive (gpsoc_create zeroes the per-solve states)
   b->p->level = 0;
@@ -1448,7 +1764,8 @@ gpsoc_status gpsoc_server_create(const gpsoc_server_opts* opts, gpsoc_server** o
   g_err.clear();
   if (!opts || !out) return fail(GPSOC_EINVAL, "NULL argument");
   if (!(opts->hbm_budget_bytes > 0)) return fail(GPSOC_EINVAL, "hbm_budget_bytes must be > 0");
-  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED) return fail(GPSOC_EINVAL, "unknown precision");
+  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED && opts->precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
   gpsoc_server* s = new gpsoc_server();
   s->opts = *opts;
   *out = s;
@@ -1485,7 +1802,8 @@ gpsoc_status gpsoc_server_submit(gpsoc_server* s, const gpsoc_grid* grid, const 
   r->psi.assign(psi0, psi0 + 2 * 3 * solve_points(r->grid));
   const int slots = s->opts.slots_per_bucket > 0 ? s->opts.slots_per_bucket : 32;
   const bool fp32_pays = (long long)slots * (long long)solve_points(r->grid) >= mixed_min_points(opts);
-  r->stage = (s->opts.precision == GPSOC_MIXED && fp32_pays) ? 1 : 2;
+  const bool lead = (s->opts.precision == GPSOC_HYBRID && hy_lead_res(opts) > 0.0);
+  r->stage = ((s->opts.precision == GPSOC_MIXED && fp32_pays) || lead) ? 1 : 2;
   s->reqs[r->ticket] = r;
   s->queue.push_back(r->ticket);
   *ticket = r->ticket;
@@ -1533,6 +1851,15 @@ gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::t
     b->in_flight = false;
     gpsoc_status st = sync_state(b->p);
     if (st != GPSOC_OK) return st;
+    if (b->hybrid) {
+      // solves that stopped are accepted on their exact FP64 residual (or resumed)
+      bool stopped = false;
+      for (size_t k = 0; k < b->slot.size(); ++k)
+        stopped |= (b->slot[k] >= 0 && !b->p->h_st[k].active && b->p->h_st[k].status == GPSOC_OK);
+      int resumed = 0;
+      if (stopped) st = hy_verify(b->p, 0, b->o, &resumed);
+      if (st != GPSOC_OK) return st;
+    }
     for (size_t k = 0; k < b->slot.size(); ++k) {
       if (b->slot[k] < 0) continue;
       const SolveState& S = b->p->h_st[k];
@@ -1541,7 +1868,7 @@ gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::t
       st = read_slot(b, (int)k, *r);
       if (st != GPSOC_OK) return st;
       b->slot[k] = -1;
-      if (b->stage == 1) {                 // FP32 stage done: continue in FP64 from this iterate
+      if (b->stage == 1) {                 // first stage done: continue in the second from this iterate
         r->fp32_iters = S.iters;
         r->stage = 2;
         s->queue.push_back(r->ticket);
@@ -1554,15 +1881,16 @@ gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::t
       o.levels = 1;
       o.beta_resets = S.beta_resets;
       o.halvings = S.halvings;
-      o.fp32_iters = r->fp32_iters;
-      o.fp64_iters = S.iters;
+      // first-stage iterations: FP32 (GPSOC_MIXED) or the FP64 lead-in (GPSOC_HYBRID)
+      o.fp32_iters = b->hybrid ? S.iters : r->fp32_iters;
+      o.fp64_iters = b->hybrid ? r->fp32_iters : S.iters;
       o.energy = S.E;
       o.mu = S.mu;
       for (int c = 0; c < 3; ++c) o.mass[c] = S.mass[c];
       o.res_inf = S.res_inf;
       o.dE_last = S.dE_last;
       o.level_iters[0] = o.total_iters;
-      o.level_fp32_iters[0] = r->fp32_iters;
+      o.level_fp32_iters[0] = o.fp32_iters;
       r->stage = 3;
     }
   }
@@ -1589,12 +1917,24 @@ gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::t
   for (Bucket* b : s->buckets) {
     for (int64_t t : b->slot) n_busy += (t >= 0);
     if (b->in_flight || bucket_empty(b)) continue;
-    const int k = (b->stage == 1) ? 1 : 0;
-    gpsoc_status st = (k == 1) ? build_graph<float>(b->p, 0, b->o) : build_graph<double>(b->p, 0, b->o);
-    if (st != GPSOC_OK) return st;
-    for (int r = 0; r < pairs; ++r) {
-      CK(cudaGraphLaunch(b->p->graph[k], b->p->stream));
-      b->p->launches += b->p->graph_kernels[k];
+    if (b->hybrid) {
+      gpsoc_status st = build_graph_hy(b->p, 0, b->o, false);
+      if (st == GPSOC_OK) st = build_graph_hy(b->p, 0, b->o, true);
+      if (st != GPSOC_OK) return st;
+      const int every = std::max(1, b->refresh / 2);
+      for (int r = 0; r < pairs; ++r) {
+        const int gk = (r % every == 0) ? 3 : 2;   // every round opens with the exact H_lin Phi
+        CK(cudaGraphLaunch(b->p->graph[gk], b->p->stream));
+        b->p->launches += b->p->graph_kernels[gk];
+      }
+    } else {
+      const int k = b->fp32_phase ? 1 : 0;
+      gpsoc_status st = (k == 1) ? build_graph<float>(b->p, 0, b->o) : build_graph<double>(b->p, 0, b->o);
+      if (st != GPSOC_OK) return st;
+      for (int r = 0; r < pairs; ++r) {
+        CK(cudaGraphLaunch(b->p->graph[k], b->p->stream));
+        b->p->launches += b->p->graph_kernels[k];
+      }
     }
     CK(cudaEventRecord(b->done, b->p->stream));
     b->in_flight = true;

@@ -85,6 +85,7 @@ struct SolveState {
   int pending;      // an accepted step waits to be applied by the next iteration's first pass
   int it_win;       // FP32 phase: iteration at which the current stall window opened
   int last_par;     // buffer parity (0/1) of the iteration whose step was accepted last
+  int upd_applied;  // the opening pass of this iteration applied the step accepted before it
   // observables of the current iterate
   double E, mu, Q;          // energy, chemical potential, <H_lin Phi, Phi>
   double rho2, F2;          // sum rho^2, sum |F|^2 (times dV)
@@ -97,6 +98,8 @@ struct SolveState {
   double a, b, theta, dE, dE_last;
   double upd_c, upd_s, upd_scale;
   double E_win;     // FP32 phase: energy when the stall window opened
+  double kin[3];    // GPSOC_HYBRID: per-component kinetic sums of the last exact recomputation of H_lin Phi
+  double acorr;     // radial part Re<P, Phi>/||Phi||^2 removed from the last direction (tangent correction)
   // FP32 copies of the scalars the array passes read (refreshed by mirror32)
   float fmu, fbeta, fcproj, fupd_c, fupd_s, fupd_scale, falpha[3], fpad;
 };
@@ -136,6 +139,8 @@ enum Slot {
   SL_DPHIINF,                                     // max |Phi_new - Phi|^2
   SL_NORM,                                        // sum |phi|^2 for normalisation
   SL_HD, SL_ZPHI, SL_HZ,                          // Re<H Phi, D>, Re<z, Phi>, Re<H Phi, z>
+  SL_KPHI0, SL_KPHI1, SL_KPHI2,                   // GPSOC_HYBRID: sum 1/2 |k|^2 |Phi_hat_l|^2
+  SL_KX0, SL_KX1, SL_KX2,                         //   and sum 1/2 |k|^2 Re(Phi_hat_l conj P_hat_l)
   NSLOT
 };
 
@@ -152,7 +157,9 @@ struct ScalarCtx {
   long long npts;
   double dV;
   OptsDev opts;
-  int flags;            // 2 = count accepted steps as FP32 iterations; bit 2 = buffer parity of the iteration
+  int flags;            // 2 = count accepted steps as FP32 iterations; bit 2 = buffer parity of the iteration;
+                        // 8 = GPSOC_HYBRID iteration (kinetic part of alpha from the state, residual-based
+                        //     slopes: the H Phi slots hold Re<r, .> sums)
   double inv_npts;      // 1 / npts
 };
 
@@ -174,6 +181,14 @@ struct ChainArgs {
   int fuse;           // the last block of the pass runs the scalar step that consumes its sums
   unsigned* cnt;      // per-solve block arrival counters (fused scalar steps)
   ScalarCtx sc;
+  // GPSOC_HYBRID passes of an FP32 chain that also read the FP64 state
+  const double2* phi64;   // Phi (FP64)
+  const double2* hl64;    // H_lin Phi (FP64)
+  // GPSOC_HYBRID, last column pass of the P chain: the spectrum of Phi (advanced by the
+  // step applied this iteration when khat_upd is set) and of the previous P, both updated
+  // in place, for the exact per-component kinetic sums of alpha
+  C* xhat; C* phat;
+  int khat_upd;
 };
 
 __device__ __forceinline__ bool gate_ok(const SolveState* st, int gate, int s) {
@@ -419,7 +434,11 @@ enum RowMode {
   ROW_INV_PRE,         // z = s * F_x^-1(in0)/npts -> out0; reduce <r,z>, <r_prev,z> (in2 = r, in3 = r_prev, in1 = Phi)
   ROW_INV_PLAIN,       // out0 = scale * F_x^-1(in0)
   ROW_INV_LIN,         // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
-  ROW_FWD_UPD          // Phi (in0, written back to out1) <- pending step with P (in2); out0 = F_x(Phi)
+  ROW_FWD_UPD,         // Phi (in0, written back to out1) <- pending step with P (in2); out0 = F_x(Phi)
+  ROW_FWD_PRE_HY,      // FP32 pass of GPSOC_HYBRID: r = H_lin Phi + nonlinear(Phi) - mu Phi in FP64 from
+                       // phi64, hl64 -> out1 (FP32); out0 = F_x(P_V^{1/2} r); reduce max|r| in FP64
+  ROW_INV_P_HY         // FP32 pass of GPSOC_HYBRID: as ROW_INV_P with in4 = r (slot HPHIP = Re<r, P>),
+                       // out0 = H_lin P, and Re<P, Phi> summed in FP64 against phi64
 };
 enum ColMode {
   COL_FWD = 0,         // out0 = F_axis(in0)

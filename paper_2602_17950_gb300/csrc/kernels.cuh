@@ -14,7 +14,8 @@ enum Phase {
   PH_STEP,          // Algorithm 2 (step model, backtracking, update coefficients)
   PH_CLEAR,         // drop the pending-step flag
   PH_NORM,          // 1/sqrt(mass) per solve into norm_scale
-  PH_MODEL          // a_n, b_n and E(theta) - E(0) at given angles into model_out
+  PH_MODEL,         // a_n, b_n and E(theta) - E(0) at given angles into model_out
+  PH_KIN            // per-component kinetic sums of the last column pass into the state (GPSOC_HYBRID)
 };
 
 struct ScalarArgs {
@@ -55,6 +56,31 @@ struct ElemArgs {
   ScalarCtx sc;
   int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
 };
+
+// GPSOC_HYBRID: the FP64 pass that opens an iteration.  HY_UPD applies the pending
+// step Phi <- s (c Phi + t P) (P in FP32), HY_REC advances H_lin Phi by the same
+// linear combination of H_lin Phi and H_lin P, HY_REDUCE forms the nonlinear terms,
+// the energy / mu / alpha / mass sums of the FP64 state, writes the FP32 copy of Phi
+// and runs the observables step in the last block of each solve.
+enum { HY_UPD = 1, HY_REC = 2, HY_REDUCE = 4 };
+struct HyArgs {
+  SolveState* st;
+  const PhysDev* phys;
+  double* part; int pmax;
+  Geo g;
+  TrapDev trap;
+  double2* phi;          // Phi (FP64), updated in place
+  double2* hl;           // H_lin Phi (FP64), updated in place
+  const float2* p;       // the pending direction P (FP32)
+  const float2* hlp;     // H_lin P (FP32)
+  float2* phi32;         // FP32 copy of Phi for the FP32 passes
+  long long npts;
+  int bps, nsolve, gate, flags;
+  int fuse;
+  unsigned* cnt;
+  ScalarCtx sc;
+};
+void launch_hy_upd(const HyArgs& a, cudaStream_t st);
 
 void launch_scalar(const ScalarArgs& a, cudaStream_t st);
 template <class T> void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st);

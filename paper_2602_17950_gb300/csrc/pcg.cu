@@ -51,6 +51,13 @@ __global__ void k_scalar(ScalarArgs A) {
     case PH_CPROJ: sc_cproj(X, s, scratch); return;
     case PH_STEP: sc_step(X, s, scratch); return;
     case PH_CLEAR: if (threadIdx.x == 0) S.pending = 0; return;
+    case PH_KIN: {
+      double kin[3];
+      const int ks[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
+      slot_totals<3>(X, s, ks, A.nb_col, kin, scratch);
+      if (threadIdx.x == 0) for (int c = 0; c < 3; ++c) S.kin[c] = kin[c];
+      return;
+    }
     case PH_MODEL: {
       SolveState L;
       if (threadIdx.x == 0) L = S;
@@ -166,6 +173,98 @@ __global__ void k_elem(ElemArgs<T> A) {
     const int slot = (MODE == EL_UPDATE) ? SL_DPHIINF : SL_NORM;
     A.part[((long long)s * NSLOT + slot) * A.pmax + rb] = v[0];
   }
+}
+
+// GPSOC_HYBRID opening pass (see HyArgs).  Same block decomposition as the row
+// passes; all arithmetic on the state in FP64.
+__global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
+  __shared__ double scratch[16 * 8 + 16];
+  __shared__ int last_flag;
+  const int bps = A.bps;
+  const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
+  if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
+  const SolveState& S = A.st[s];
+  const long long npts = A.npts;
+  const long long per = npts / bps;
+  const long long sbase = (long long)s * 3 * npts, ebase = (long long)rb * per;
+  const bool upd = (A.flags & HY_UPD) && S.pending;
+  const bool rec = upd && (A.flags & HY_REC);
+  const bool red = (A.flags & HY_REDUCE) != 0;
+  const double uc = S.upd_c, us = S.upd_s, usc = S.upd_scale;
+  const PhysDev ph = A.phys[s];
+  const int nx = A.g.n[0], ny = A.g.n[1];
+  double acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+  double dmax = 0.0;
+  for (long long e = threadIdx.x; e < per; e += blockDim.x) {
+    const long long off = ebase + e;
+    double2 f[3], hl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long i = sbase + c * npts + off;
+      f[c] = A.phi[i];
+      if (red) hl[c] = A.hl[i];
+      if (upd) {
+        // the accepted step (Eqs. formula-pcg, update) with the exact tangent direction
+        const float2 q = A.p[i];
+        const double2 o = make_double2(usc * (uc * f[c].x + us * (double)q.x), usc * (uc * f[c].y + us * (double)q.y));
+        const double dr = o.x - f[c].x, di = o.y - f[c].y;
+        dmax = fmax(dmax, dr * dr + di * di);
+        A.phi[i] = o;
+        f[c] = o;
+        if (rec) {
+          // H_lin is linear: H_lin Phi' = s (c H_lin Phi + t H_lin P)
+          const double2 h0 = A.hl[i];
+          const float2 hq = A.hlp[i];
+          const double2 h1 = make_double2(usc * (uc * h0.x + us * (double)hq.x), usc * (uc * h0.y + us * (double)hq.y));
+          A.hl[i] = h1;
+          hl[c] = h1;
+        }
+      }
+    }
+    if (!red) continue;
+    // energy pieces of Eq. energy with H_lin Phi given: <H_lin Phi, Phi>, rho^2, |F|^2, and
+    // the alpha_l pieces V |phi_l|^2, rho |phi_l|^2 (Eq. PreCnstAlpha), masses
+    const long long row = off / nx;
+    const double V = trap_value<double>(A.trap, A.g, (int)(off - row * nx), (int)(row % ny), (int)(row / ny), off);
+    double m[3], rho = 0.0, q = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m[c] = f[c].x * f[c].x + f[c].y * f[c].y;
+      rho += m[c];
+      q += f[c].x * hl[c].x + f[c].y * hl[c].y;
+      A.phi32[sbase + c * npts + off] = make_float2((float)f[c].x, (float)f[c].y);
+    }
+    const double ar = f[1].x * f[0].x + f[1].y * f[0].y + f[2].x * f[1].x + f[2].y * f[1].y;
+    const double ai = f[1].x * f[0].y - f[1].y * f[0].x + f[2].x * f[1].y - f[2].y * f[1].x;
+    const double Fz = m[0] - m[2];
+    acc[0] += q;
+    acc[1] += rho * rho;
+    acc[2] += 2.0 * (ar * ar + ai * ai) + Fz * Fz;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[3 + c] += V * m[c];
+      acc[6 + c] += rho * m[c];
+      acc[9 + c] += m[c];
+    }
+  }
+  double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
+  if (upd) {
+    double v1[1] = {dmax};
+    const bool mx1[1] = {true};
+    block_reduce<1>(v1, scratch, mx1);
+    if (threadIdx.x == 0) P[(long long)SL_DPHIINF * A.pmax] = v1[0];
+  }
+  if (!red) return;
+  const bool mx[12] = {};
+  block_reduce<12>(acc, scratch, mx);
+  if (threadIdx.x == 0) {
+    const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) P[(long long)slots[k] * A.pmax] = acc[k];
+  }
+  if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, scratch);
 }
 
 // zero-pad the full spectrum of level N (in) into level 2N (out, zeroed first)
@@ -289,6 +388,8 @@ __global__ void k_comp_scale(double2* data, long long npts, const double* mass, 
 
 // ------------------------------------------------------------------ launchers
 void launch_scalar(const ScalarArgs& a, cudaStream_t st) { k_scalar<<<a.nsolve, kScalarThreads, 0, st>>>(a); }
+
+void launch_hy_upd(const HyArgs& a, cudaStream_t st) { k_hy_upd<<<a.bps * a.nsolve, 256, 0, st>>>(a); }
 
 template <class T>
 void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st) {

@@ -78,6 +78,7 @@ __device__ __forceinline__ void obs_update(const ScalarCtx& X, int s, SolveState
   const double floor_a = 1e-12 * amax + 1e-300;
   for (int c = 0; c < 3; ++c) S.alpha[c] = fmax(S.alpha[c], floor_a);
   if (had_step) S.dphi_inf = sqrt(dphi);
+  S.upd_applied = had_step ? 1 : 0;
   S.pending = 0;
   if (!isfinite(S.E) || !isfinite(S.mu) || !isfinite(S.alpha[0] + S.alpha[1] + S.alpha[2]))
     deactivate(S, GPSOC_ENONFINITE);
@@ -89,10 +90,16 @@ __device__ __forceinline__ void sc_obs(const ScalarCtx& X, int s, double* scratc
   __shared__ SolveState sS;
   state_load(sS, X.st + s);      // visible after the barrier that opens the first reduction
   double kin[3], v[12];
-  const int kslots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
-  slot_totals<3>(X, s, kslots, X.nb_col, kin, scratch);
+  if (!(X.flags & 8)) {
+    const int kslots[3] = {SL_KIN0, SL_KIN1, SL_KIN2};
+    slot_totals<3>(X, s, kslots, X.nb_col, kin, scratch);
+  }
   const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
   slot_totals<12>(X, s, slots, X.nb_row, v, scratch);
+  // GPSOC_HYBRID: the kinetic part of alpha_l is that of the last exact FP64 recomputation
+  // of H_lin Phi (alpha only shifts the preconditioner; the fixed point does not depend on it)
+  if (X.flags & 8)
+    for (int c = 0; c < 3; ++c) kin[c] = sS.kin[c];
   const bool had_step = sS.pending != 0;
   double dphi = 0.0;
   if (had_step) dphi = slot_max(X, s, SL_DPHIINF, X.nb_row, scratch);
@@ -168,7 +175,10 @@ __device__ __forceinline__ void sc_cproj(const ScalarCtx& X, int s, double* scra
   if (threadIdx.x != 0) return;
   const double dV = X.dV;
   const double cD = dV * w[0], hD = dV * w[1];
-  if (S.beta != 0.0 && !(hD - cD * S.mu < 0.0)) {
+  // slope of the projected direction: Re<H Phi, D> - c mu, or in GPSOC_HYBRID (whose
+  // pass sums Re<r, D> with the FP64-accurate residual r) Re<r, D> itself
+  const double slope = (X.flags & 8) ? hD : hD - cD * S.mu;
+  if (S.beta != 0.0 && !(slope < 0.0)) {
     S.beta = 0.0;
     S.beta_resets++;
     S.cproj = -dV * w[2];   // D = -z: Re<D, Phi> = -Re<z, Phi>
@@ -228,10 +238,35 @@ __device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scr
   slot_totals<14>(X, s, slots, X.nb_row, v, scratch);
   if (threadIdx.x != 0) return;
   const double dV = X.dV;
-  S.P2 = dV * v[0]; S.HPP = dV * v[1]; S.HPhiP = dV * v[2]; S.RPhi = dV * v[3];
-  for (int k = 0; k < 5; ++k) { S.I[k + 1] = dV * v[4 + k]; S.J[k + 1] = dV * v[9 + k]; }
-  S.I[0] = S.rho2; S.J[0] = S.F2;
   const PhysDev ph = X.phys[s];
+  const double c0 = ph.c0, c1 = ph.c1;
+  const double P2 = dV * v[0], HPP = dV * v[1], X1 = dV * v[2], RPhi = dV * v[3];
+  double I[6], J[6];
+  I[0] = S.rho2; J[0] = S.F2;
+  for (int k = 0; k < 5; ++k) { I[k + 1] = dV * v[4 + k]; J[k + 1] = dV * v[9 + k]; }
+  const double M = S.mass[0] + S.mass[1] + S.mass[2];
+  // Re<H_lin Phi, P>: from Re<H Phi, P>, or in GPSOC_HYBRID from Re<r, P> + mu Re<P, Phi>
+  const double QFP = ((X.flags & 8) ? X1 + S.mu * RPhi : X1) - c0 * I[1] - c1 * J[1];
+  // Exact tangent correction: the step is taken along P_t = P - a Phi, a = Re<P, Phi>/||Phi||^2,
+  // which is tangent to the sphere whatever the rounding of P (an FP32 direction carries a
+  // radial part of relative size 1e-7).  Every sum transforms exactly: R -> R - a rho_Phi,
+  // rho_P -> rho_P - 2a R + a^2 rho_Phi, and the same for the spin vectors.
+  const double a = RPhi / M, a2 = a * a;
+  S.acorr = a;
+  S.P2 = P2 - a * RPhi;
+  S.HPP = HPP - 2.0 * a * QFP + a2 * S.Q;
+  S.RPhi = 0.0;
+  for (int t = 0; t < 2; ++t) {
+    const double* Y = t ? J : I;
+    double* Z = t ? S.J : S.I;
+    Z[0] = Y[0];
+    Z[1] = Y[1] - a * Y[0];
+    Z[2] = Y[2] - 2.0 * a * Y[1] + a2 * Y[0];
+    Z[3] = Y[3] - 2.0 * a * Y[1] + a2 * Y[0];
+    Z[4] = Y[4] - 2.0 * a * Y[3] - a * Y[2] + 3.0 * a2 * Y[1] - a2 * a * Y[0];
+    Z[5] = Y[5] + 4.0 * a2 * Y[3] + a2 * a2 * Y[0] - 4.0 * a * Y[4] + 2.0 * a2 * Y[2] - 4.0 * a2 * a * Y[1];
+  }
+  S.HPhiP = (QFP - a * S.Q) + c0 * S.I[1] + c1 * S.J[1];
   pn = p_norm(S.P2);
   // density frozen at Phi^n in H_l(P^n)
   S.a = -S.mu + (S.HPP + ph.c0 * S.I[2] + ph.c1 * S.J[2] + 2.0 * (ph.c0 * S.I[3] + ph.c1 * S.J[3])) * pn.inv_nP2;
@@ -278,8 +313,9 @@ __device__ __forceinline__ void step_decide(const ScalarCtx& X, int s, SolveStat
   S.dE_last = dE;
   const double sp = sn * pn.inv_nP;
   const double M = S.mass[0] + S.mass[1] + S.mass[2];
-  const double nrm2 = cs * cs * M + 2.0 * cs * sp * S.RPhi + sp * sp * S.P2;
-  S.upd_c = cs; S.upd_s = sp; S.upd_scale = rsqrt(nrm2);
+  // Phi' = (cos t Phi + sin t P_t/|P_t|)/norm with P_t = P - a Phi tangent: |.|^2 = c^2 M + s'^2 |P_t|^2
+  const double nrm2 = cs * cs * M + sp * sp * S.P2;
+  S.upd_c = cs - sp * S.acorr; S.upd_s = sp; S.upd_scale = rsqrt(nrm2);
   S.pending = 1;
   S.last_par = (X.flags >> 2) & 1;
   S.iters++; S.total_iters++;
@@ -292,9 +328,23 @@ __device__ __forceinline__ void sc_step(const ScalarCtx& X, int s, double* scrat
   __shared__ SolveState sS;
   state_load(sS, X.st + s);      // visible after the barrier that opens the reduction
   PNorm pn;
+  double kq[9];
+  if (X.flags & 8) {
+    // GPSOC_HYBRID: kinetic sums of Phi, of P and their cross term from the column pass
+    const int ks[9] = {SL_KPHI0, SL_KPHI1, SL_KPHI2, SL_KX0, SL_KX1, SL_KX2, SL_KIN0, SL_KIN1, SL_KIN2};
+    slot_totals<9>(X, s, ks, X.nb_col, kq, scratch);
+  }
   step_sums(X, s, scratch, sS, pn);
   if (threadIdx.x == 0) {
     step_decide(X, s, sS, pn);
+    if (X.flags & 8) {
+      // kinetic part of alpha_l at the next iterate, exactly: Phi' = g (c Phi + t P), so
+      // |k|^2 |Phi'_hat|^2 sums to g^2 (c^2 K_Phi + 2 c t K_x + t^2 K_P) per component
+      const bool acc = sS.pending != 0;
+      const double g2 = sS.upd_scale * sS.upd_scale, c = sS.upd_c, t = sS.upd_s;
+      for (int l = 0; l < 3; ++l)
+        sS.kin[l] = acc ? g2 * (c * c * kq[l] + 2.0 * c * t * kq[3 + l] + t * t * kq[6 + l]) : kq[l];
+    }
     mirror32(sS);
   }
   __syncthreads();

@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgpsoc.so")
 
-GPSOC_FP64, GPSOC_MIXED = 0, 1
+GPSOC_FP64, GPSOC_MIXED, GPSOC_HYBRID = 0, 1, 2
 GPSOC_STOP_DPHI, GPSOC_STOP_RES, GPSOC_STOP_ENERGY = 1, 2, 3
 TRAP_HARMONIC, TRAP_HARMONIC_QUARTIC, TRAP_USER = 0, 1, 2
 _STATUS = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ENONFINITE", "ETIMEOUT", "ESTATE", "EBUDGET",
@@ -51,7 +51,8 @@ class Opts(C.Structure):
                 ("max_iter", C.c_int), ("theta_trial", C.c_double), ("sigma", C.c_double),
                 ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int),
                 ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int), ("precond", C.c_int),
-                ("fp32_res_switch", C.c_double), ("fp32_carry", C.c_int)]
+                ("fp32_res_switch", C.c_double), ("fp32_carry", C.c_int), ("hybrid_refresh", C.c_int),
+                ("hybrid_lead_res", C.c_double)]
 
 
 class Result(C.Structure):
@@ -236,10 +237,12 @@ class Problem:
     @staticmethod
     def opts(precision=GPSOC_FP64, stop=GPSOC_STOP_ENERGY, tol=1e-12, res_tol=0.0, max_iter=100000,
              theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0, fp32_switch=0.0,
-             fp32_min_points=0, precond="combined", fp32_res_switch=0.0, fp32_carry=0):
+             fp32_min_points=0, precond="combined", fp32_res_switch=0.0, fp32_carry=0, hybrid_refresh=0,
+             hybrid_lead_res=0.0):
         pk = PRECONDS.index(precond) if isinstance(precond, str) else int(precond)
         return Opts(precision, stop, tol, res_tol, max_iter, theta_trial, sigma, max_halvings, cm_levels,
-                    check_every, fp32_switch, fp32_min_points, pk, fp32_res_switch, int(fp32_carry))
+                    check_every, fp32_switch, fp32_min_points, pk, fp32_res_switch, int(fp32_carry),
+                    int(hybrid_refresh), float(hybrid_lead_res))
 
     # -------------------------------------------------------------- state
     def set_initial(self, psi: np.ndarray, level=0):
