@@ -337,6 +337,53 @@ class Model:
             inter = inter + 0.5 * self.c1 * dF * (2 * Ff[a] + dF)
         return quad + self.grid.integrate(inter)
 
+    def trig_form(self, Phi, Phat):
+        """E(cos(t) Phi + sin(t) Phat) - E(Phi) and its t-derivative as explicit functions of t
+        (Section 3.1, the rewrite of E(theta) in sin and cos whose coefficients are integrals).
+
+        With c = cos t, s = sin t the combination's coefficients are u = c^2 - 1 = -s^2 on the
+        Phi-Phi terms, v = 2cs on the Phi-Phat cross terms and w = s^2 on the Phat-Phat terms:
+          quadratic part  u <H_lin Phi, Phi> + v Re<H_lin Phi, Phat> + w <H_lin Phat, Phat>
+          rho_t - rho     = u rho_Phi + v R + w rho_Phat,   R = Re sum_l conj(phi_l) phat_l
+          F_t - F         = u F(Phi) + v Re F~(Phi, Phat) + w F(Phat)
+          interaction     c0/2 int (rho_t - rho)(rho_t + rho) + c1/2 int (F_t - F).(F_t + F)
+        so Delta E is a quadratic polynomial in (u, v, w) whose coefficients are integrals of
+        Phi and Phat computed here once; du/dt = -sin 2t, dv/dt = 2 cos 2t, dw/dt = sin 2t.
+        Returns (dE(t), dE'(t)) as functions of t."""
+        g = self.grid
+        HF, HP = self.H_lin(Phi), self.H_lin(Phat)
+        l1 = {"u": self.inner(HF, Phi).real, "v": self.inner(HF, Phat).real, "w": self.inner(HP, Phat).real}
+        _, rf = self.densities(Phi)
+        _, rp = self.densities(Phat)
+        R = np.real(np.sum(np.conj(Phi) * Phat, axis=0))
+        dens = {"u": rf, "v": R, "w": rp}
+        Ff, Fp, Fx = self.spin_vector(Phi), self.spin_vector(Phat), self.Ftilde(Phi, Phat)
+        spin = {"u": Ff, "v": tuple(np.real(f) for f in Fx), "w": Fp}
+        keys = ("u", "v", "w")
+        # linear coefficient of each variable and the symmetric quadratic coefficients
+        lin = {k: l1[k] + self.c0 * g.integrate(rf * dens[k])
+               + self.c1 * g.integrate(sum(Ff[a] * spin[k][a] for a in range(3))) for k in keys}
+        quad = {(i, j): 0.5 * self.c0 * g.integrate(dens[i] * dens[j])
+                + 0.5 * self.c1 * g.integrate(sum(spin[i][a] * spin[j][a] for a in range(3)))
+                for i in keys for j in keys}
+
+        def parts(t):
+            c, s = math.cos(t), math.sin(t)
+            x = {"u": -s * s, "v": 2 * c * s, "w": s * s}
+            dx = {"u": -math.sin(2 * t), "v": 2 * math.cos(2 * t), "w": math.sin(2 * t)}
+            return x, dx
+
+        def dE(t):
+            x, _ = parts(t)
+            return (sum(lin[k] * x[k] for k in keys)
+                    + sum(quad[(i, j)] * x[i] * x[j] for i in keys for j in keys))
+
+        def dE1(t):
+            x, dx = parts(t)
+            return (sum(lin[k] * dx[k] for k in keys)
+                    + sum(quad[(i, j)] * (dx[i] * x[j] + x[i] * dx[j]) for i in keys for j in keys))
+        return dE, dE1
+
     # ------------------------------------------------------------------ preconditioners (Section 3.4)
     def alpha(self, Phi):
         """alpha_l = integral 1/2|grad phi_l|^2 + V|phi_l|^2 + c0 rho |phi_l|^2 (Eq. PreCnstAlpha), R-ALPHA."""

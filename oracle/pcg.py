@@ -30,6 +30,8 @@ Readings (written independently on the CUDA side):
            energy change, R-DE; equal to E(Phi^n) - E(Phi^{n-1}) up to rounding), stop2
            max_l ||r_l^n||_inf < tol, stop1 max_l ||phi_l^n - phi_l^{n-1}||_inf
            < tol.  `res_tol`, if set, additionally requires ||r^n||_inf < res_tol.
+  R-EXACT  line_search="exact" solves Eq. theta instead of the quadratic model (see
+           exact_theta); Algorithm 2's acceptance test and halvings still apply.
   R-CM     interpolation between levels is spectral zero padding: coefficient
            p in [-N/2, N/2-1] is placed at the same p on the 2N grid, the result
            is scaled by 2^d and renormalised to unit mass; each level restarts
@@ -56,6 +58,7 @@ class Options:
     sigma: float = 0.5
     max_halvings: int = 40
     precond: str = "combined"     # "combined" (Eq. PreCondMix), "kinetic", "potential", "none"
+    line_search: str = "model"    # "model": Algorithm 2's quadratic model; "exact": Eq. theta (R-EXACT)
 
 
 @dataclass
@@ -83,6 +86,23 @@ def _apply_precond(model: Model, kind: str, r, Phi, alpha):
     if kind == "none":
         return r.copy()
     raise ValueError(kind)
+
+
+def exact_theta(model: Model, Phi, Phat, t0: float) -> float:
+    """theta_n = argmin_{theta > 0} E(cos(theta) Phi + sin(theta) Phat) (Eq. theta), on the
+    explicit sin/cos form of E(theta) (Section 3.1).  R-EXACT: E(theta) has period pi (the
+    energy does not see the sign of the wave function) and decreases at 0+; the minimiser
+    taken is the first zero of dE/dtheta found by doubling from the quadratic model's theta
+    t0 (a bracket [lo, hi] with dE/dtheta(lo) < 0 <= dE/dtheta(hi), hi <= pi), solved to
+    rounding by Brent's root finder.  If no sign change is met up to pi, t0 is kept."""
+    from scipy.optimize import brentq
+    _, g = model.trig_form(Phi, Phat)
+    lo, hi = 0.0, min(t0, math.pi)
+    while g(hi) < 0.0 and hi < math.pi:
+        lo, hi = hi, min(2.0 * hi, math.pi)
+    if g(hi) < 0.0:
+        return t0
+    return brentq(g, lo, hi, xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)
 
 
 def normalize(model: Model, Phi):
@@ -147,6 +167,8 @@ def pcg(model: Model, Phi0, opts: Options = Options(), callback=None) -> Result:
         if status == "stagnated":
             break
         Phat = P / math.sqrt(model.mass(P))
+        if opts.line_search == "exact":
+            theta = exact_theta(model, Phi, Phat, theta)
         # Algorithm 2, Steps 3-4
         accepted = False
         for _ in range(opts.max_halvings + 1):

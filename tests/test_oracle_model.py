@@ -329,3 +329,50 @@ def test_combined_preconditioner_and_alpha_closed_form_on_uniform_density(n, L):
         q2 = sum((math.pi * qw[c][i] / L[i]) ** 2 for i in range(d))
         fac = 1.0 / ((alpha[c] + c0 * rho) * (alpha[c] + 0.5 * q2))
         np.testing.assert_allclose(z[c], fac * r[c], rtol=1e-12, atol=1e-15)
+
+
+def test_trig_form_is_the_energy_change_and_its_derivative():
+    # Section 3.1: E(cos t Phi + sin t Phat) - E(Phi) written out in sin/cos with precomputed
+    # integrals equals the direct difference of two energies; its derivative equals the finite
+    # difference of the direct form and, at t = 0, the slope 2 Re<H(Phi), Phat>
+    m = _model((32, 32), (6.0, 6.0), Omega=0.55, gamma=0.9, c0=25.0, c1=-4.0)
+    Phi = _smooth(m, 16)
+    Phi = Phi / math.sqrt(m.mass(Phi))
+    D = _smooth(m, 17)
+    P = D - m.inner(D, Phi).real * Phi
+    Ph = P / math.sqrt(m.mass(P))
+    dE, dE1 = m.trig_form(Phi, Ph)
+    E0 = m.energy(Phi)
+    for t in (2.9, 1.3, 0.4, 0.05):
+        direct = m.energy(math.cos(t) * Phi + math.sin(t) * Ph) - E0
+        assert dE(t) == pytest.approx(direct, rel=1e-9, abs=1e-12)
+        h = 1e-4
+        fd = (m.energy_change(Phi, Ph, t + h) - m.energy_change(Phi, Ph, t - h)) / (2 * h)
+        assert dE1(t) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    assert dE1(0.0) == pytest.approx(2 * m.inner(m.H(Phi), Ph).real, rel=1e-12)
+    assert dE(math.pi) == pytest.approx(0.0, abs=1e-12)            # period pi: E(-Phi) = E(Phi)
+
+
+def test_exact_theta_minimises_the_energy_along_the_curve():
+    # Eq. theta: the exact step is a stationary point with lower energy than the quadratic
+    # model's step and than its neighbours
+    from oracle.pcg import exact_theta
+    m = _model((32, 32), (6.0, 6.0), Omega=0.5, gamma=0.5, c0=100.0, c1=-1.0)
+    Phi = _smooth(m, 20)
+    Phi = Phi / math.sqrt(m.mass(Phi))
+    H = m.H(Phi)
+    mu = m.mu(Phi, H)
+    r = H - mu * Phi
+    Pr = m.precond_C(r, Phi, m.alpha(Phi))
+    P = -Pr - m.inner(-Pr, Phi).real * Phi
+    a, b = m.step_coefficients(Phi, P, H, mu)
+    Ph = P / math.sqrt(m.mass(P))
+    assert b < 0
+    tq = -b / (2 * a) if a > 0 else 0.1          # Algorithm 2's starting step
+    t = exact_theta(m, Phi, Ph, tq)
+    assert t > 0
+    dE, dE1 = m.trig_form(Phi, Ph)
+    assert abs(dE1(t)) < 1e-10 * abs(dE1(0.0))
+    assert dE(t) <= dE(tq) + 1e-15
+    for s in (0.9, 1.1):
+        assert dE(t) < dE(s * t)
