@@ -128,7 +128,12 @@ typedef struct {
  *                FP64 iterations until max_l ||r_l||_inf < hybrid_lead_res (the early
  *                iterations from the initial guess decide which local minimum is
  *                reached), then the hybrid ones; finer levels are hybrid throughout.
- *                0 selects 1e-4, a negative value runs no FP64 lead-in. */
+ *                0 selects 1e-4, a negative value runs no FP64 lead-in.
+ *   line_search  0: the step size of Algorithm 2 (minimiser of the quadratic model
+ *                of Eqs. approeng-bn); 1: the minimiser of Eq. theta on the explicit
+ *                sin/cos form of E(theta) (the first zero of dE/dtheta bracketed by
+ *                doubling from the model's step, Newton steps kept in the bracket);
+ *                Algorithm 2's acceptance test and halvings apply to both. */
 typedef struct {
   int precision;
   int stop;
@@ -146,6 +151,7 @@ typedef struct {
   int fp32_carry;
   int hybrid_refresh;
   double hybrid_lead_res;
+  int line_search;
 } gpsoc_opts;
 
 /* Per-solve result.  energy, mu, mass[] describe the final iterate;
@@ -324,6 +330,30 @@ uint64_t gpsoc_kernel_launches(const gpsoc_problem* p);
  * passes), *threads = threads per block. */
 gpsoc_status gpsoc_tile_shape(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
                               int* elems_per_thread, int* threads);
+
+/* Tile autotuning (no counterpart in the paper).  Tiles are chosen per grid,
+ * batch size and kernel precision (FP64 kernels for GPSOC_FP64, FP32 kernels for
+ * GPSOC_MIXED and GPSOC_HYBRID) from a process-wide table; keys without an entry
+ * use the built-in rule (the largest tile that still gives at least two blocks
+ * per SM).  Every problem with the same grid, batch and precision uses the table
+ * entry, which sets all passes along an axis together.
+ *   gpsoc_tile_candidates: the valid (lines, elems_per_thread) tiles of an axis on
+ *     a level: lines a power of two, elems_per_thread a supported radix (2, 4, 8,
+ *     and 16 for FP32 column passes), at most 384 threads and 200 KB of shared
+ *     memory per block.  Writes min(count, cap) pairs; *count = all of them.
+ *   gpsoc_tuning_set: set the tile of an axis for this problem's grid (at `level`),
+ *     batch and precision; lines = 0 returns the axis to the rule; EINVAL if the
+ *     tile is not a candidate.  The problem's captured graphs are dropped.
+ *   gpsoc_autotune: on the current level, time every candidate of each axis
+ *     (CUDA events over `iters` profiled iterations of opts->precision, each from
+ *     the same state) against the rule and keep the fastest; lines[3] and
+ *     elems_per_thread[3] (may be NULL) receive the tiles now in use (0 beyond
+ *     dim).  The state is restored afterwards but iteration counters are reset. */
+gpsoc_status gpsoc_tile_candidates(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
+                                   int* elems_per_thread, int cap, int* count);
+gpsoc_status gpsoc_tuning_set(const gpsoc_problem* p, int level, int axis, int precision, int lines,
+                              int elems_per_thread);
+gpsoc_status gpsoc_autotune(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int* lines, int* elems_per_thread);
 
 /* Arithmetic roofline probe (no counterpart in the paper): FP64 and FP32 FMA
  * throughput of the current device in TFLOP/s (an FMA counts 2 flops), from

@@ -16,6 +16,9 @@
 // the y D_x piece is folded into the spectral-in-x array before the last x
 // inverse (y is constant along an x row), the x D_y piece is carried as a
 // second array G = F_y^{-1}[v_y F_y A] and multiplied by x after the x inverse.
+#include <map>
+#include <mutex>
+
 #include "gpsoc_internal.cuh"
 #include "scalar.cuh"
 #include "fft.cuh"
@@ -763,8 +766,41 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
 // while large batches keep long coalesced line segments.
 static constexpr int kTargetBlocks = 304;   // two blocks per SM of a 152-SM GB300
 
+// Tuned tiles (gpsoc_tuning_set / gpsoc_autotune) override the rule below for one
+// grid, batch and precision; every launch and every block count of that key reads the
+// same table entry, so the passes feeding one fused scalar step always agree.
+namespace {
+struct TileKey {
+  int n0, n1, n2, nsolve, fp32;
+  bool operator<(const TileKey& o) const {
+    if (n0 != o.n0) return n0 < o.n0;
+    if (n1 != o.n1) return n1 < o.n1;
+    if (n2 != o.n2) return n2 < o.n2;
+    if (nsolve != o.nsolve) return nsolve < o.nsolve;
+    return fp32 < o.fp32;
+  }
+};
+struct TileEntry { int lines[3] = {0, 0, 0}, ept[3] = {0, 0, 0}; };
+std::map<TileKey, TileEntry> g_tiles;
+std::mutex g_tiles_mu;
+
+template <class T> TileKey tile_key(const Geo& g, int nsolve) {
+  return TileKey{g.n[0], g.n[1], g.n[2], nsolve, sizeof(T) == 4 ? 1 : 0};
+}
+// tuned (lines, ept) of an axis, or (0, 0)
+template <class T> void tuned(const Geo& g, int axis, int nsolve, int& lines, int& ept) {
+  std::lock_guard<std::mutex> lk(g_tiles_mu);
+  auto it = g_tiles.find(tile_key<T>(g, nsolve));
+  lines = 0; ept = 0;
+  if (it != g_tiles.end()) { lines = it->second.lines[axis]; ept = it->second.ept[axis]; }
+}
+}  // namespace
+
 template <class T>
 int row_rows_per_block(const Geo& g, int nsolve) {
+  int tl, te;
+  tuned<T>(g, 0, nsolve, tl, te);
+  if (tl > 0) return tl;
   const int nx = g.n[0];
   const int rows = (int)(g.npts / nx);
   int R = 512 / nx;
@@ -776,6 +812,9 @@ int row_rows_per_block(const Geo& g, int nsolve) {
 
 template <class T>
 int col_tc(const Geo& g, int axis, int nsolve) {
+  int tl, te;
+  tuned<T>(g, axis, nsolve, tl, te);
+  if (tl > 0) return tl;
   const int na = g.n[axis];
   const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
   const int no = (int)(g.npts / ((long long)na * ni));
@@ -803,10 +842,20 @@ static int round_threads(int t) {
 }
 
 template <class T>
+static int row_ept(const Geo& g, int nsolve) {
+  int tl, te;
+  tuned<T>(g, 0, nsolve, tl, te);
+  if (tl > 0 && te > 0) return te;
+  return pick_ept<T>(3 * row_rows_per_block<T>(g, nsolve) * g.n[0], g.n[0], false);
+}
+
+template <class T>
 static void col_cfg(const Geo& g, int axis, int nsolve, int& tc, int& ept, int& threads) {
   tc = col_tc<T>(g, axis, nsolve);
   const int work = 3 * tc * g.n[axis];
-  ept = pick_ept<T>(work, g.n[axis]);
+  int tl, te;
+  tuned<T>(g, axis, nsolve, tl, te);
+  ept = (tl > 0 && te > 0) ? te : pick_ept<T>(work, g.n[axis]);
   threads = round_threads(work / ept);
 }
 
@@ -814,11 +863,62 @@ template <class T>
 void tile_shape(const Geo& g, int axis, int nsolve, int& lines, int& ept, int& threads) {
   if (axis == 0) {
     lines = row_rows_per_block<T>(g, nsolve);
-    ept = pick_ept<T>(3 * lines * g.n[0], g.n[0], false);
+    ept = row_ept<T>(g, nsolve);
     threads = round_threads(3 * lines * g.n[0] / ept);
   } else {
     col_cfg<T>(g, axis, nsolve, lines, ept, threads);
   }
+}
+
+// A tile (lines, ept) for the passes along `axis` is valid when the FFT layout fits
+// (ept a supported radix no longer than the line; every line of the tile has its
+// threads), the block stays within the kernels' thread bound and the shared memory
+// of its largest mode stays within the attribute chain_prepare sets.
+template <class T>
+bool tile_valid(const Geo& g, int axis, int lines, int ept) {
+  using C = cx_t<T>;
+  const int n = g.n[axis];
+  if (lines < 1 || (lines & (lines - 1)) || n < 2) return false;
+  const bool r16 = (sizeof(T) == 4 && axis > 0);
+  if (!(ept == 2 || ept == 4 || ept == 8 || (ept == 16 && r16)) || ept > n) return false;
+  const long long work = 3LL * lines * n;
+  if (work / ept > kThreads) return false;
+  size_t sm;
+  if (axis == 0) {
+    const int rows = (int)(g.npts / n);
+    if (lines > rows) return false;
+    sm = sizeof(C) * (fft_padded_len<C>(n) + 6 * (size_t)lines * fft_padded_len<C>(n)) + kRedDoubles * sizeof(double);
+  } else {
+    const int ni = (axis == 1) ? g.n[0] : g.n[0] * g.n[1];
+    if (lines > ni) return false;
+    sm = sizeof(C) * (fft_padded_len<C>(n) + 6 * (size_t)lines * col_line_len<C>(n, lines)) + kRedDoubles * sizeof(double);
+  }
+  return sm <= 200 * 1024;
+}
+
+// set (lines > 0) or clear (lines = 0) the tuned tile of one axis
+template <class T>
+bool tile_set(const Geo& g, int nsolve, int axis, int lines, int ept) {
+  if (axis < 0 || axis >= g.d) return false;
+  if (lines > 0 && !tile_valid<T>(g, axis, lines, ept)) return false;
+  std::lock_guard<std::mutex> lk(g_tiles_mu);
+  TileEntry& e = g_tiles[tile_key<T>(g, nsolve)];
+  e.lines[axis] = lines > 0 ? lines : 0;
+  e.ept[axis] = lines > 0 ? ept : 0;
+  return true;
+}
+
+// every valid tile of an axis: powers of two for the lines, each supported radix
+template <class T>
+int tile_candidates(const Geo& g, int axis, int* lines, int* ept, int cap) {
+  int k = 0;
+  for (int l = 1; l <= 4096; l <<= 1)
+    for (int e = 2; e <= 16; e <<= 1)
+      if (tile_valid<T>(g, axis, l, e)) {
+        if (k < cap) { lines[k] = l; ept[k] = e; }
+        ++k;
+      }
+  return k;
 }
 
 template <class T>
@@ -858,7 +958,7 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int R = row_rows_per_block<T>(a.g, a.nsolve);
   const int nb = row_blocks_per_solve<T>(a.g, a.nsolve) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE, a.nsolve);
-  const int ept = pick_ept<T>(3 * R * a.g.n[0], a.g.n[0], false);
+  const int ept = row_ept<T>(a.g, a.nsolve);
   if constexpr (row_lean<T, MODE>())
     k_row_lean<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
   else
@@ -926,6 +1026,10 @@ template void launch_row<double>(int, const ChainArgs<double>&, int, const Launc
 template void launch_row<float>(int, const ChainArgs<float>&, int, const Launch&, cudaStream_t);
 template void launch_col<double>(int, int, const ChainArgs<double>&, const Launch&, cudaStream_t);
 template void launch_col<float>(int, int, const ChainArgs<float>&, const Launch&, cudaStream_t);
+template bool tile_set<double>(const Geo&, int, int, int, int);
+template bool tile_set<float>(const Geo&, int, int, int, int);
+template int tile_candidates<double>(const Geo&, int, int*, int*, int);
+template int tile_candidates<float>(const Geo&, int, int*, int*, int);
 template void tile_shape<double>(const Geo&, int, int, int&, int&, int&);
 template void tile_shape<float>(const Geo&, int, int, int&, int&, int&);
 template int row_blocks_per_solve<double>(const Geo&, int);

@@ -318,7 +318,7 @@ ElemArgs<T> elem_args(gpsoc_problem* p, const Geo& g, int gate) {
   e.part = p->d_part;
   e.pmax = p->pmax;
   e.npts = g.npts;
-  e.bps = row_blocks_per_solve<double>(g, p->batch);
+  e.bps = row_blocks_per_solve<T>(g, p->batch);
   e.nsolve = p->batch;
   e.gate = gate;
   e.scalev = p->d_scale;
@@ -460,6 +460,7 @@ OptsDev make_opts(const gpsoc_opts* o) {
   d.no_stop = 0;
   d.precond = o->precond;
   d.res32 = o->fp32_res_switch > 0 ? o->fp32_res_switch : 0.0;
+  d.line_search = o->line_search == 1 ? 1 : 0;
   return d;
 }
 
@@ -571,7 +572,7 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
   h.hlp = p->b32.HPhi;                // its H_lin P
   h.phi32 = p->b32.Phi;
   h.npts = g.npts;
-  h.bps = row_blocks_per_solve<double>(g, p->batch);
+  h.bps = row_blocks_per_solve<float>(g, p->batch);   // the fused tail reads FP32 tile counts
   h.nsolve = p->batch;
   h.gate = gate;
   h.flags = flags;
@@ -1527,14 +1528,109 @@ const char* gpsoc_profile_name(const gpsoc_problem* p, int k) {
 
 uint64_t gpsoc_kernel_launches(const gpsoc_problem* p) { return p ? p->launches : 0; }
 
+gpsoc_status gpsoc_tile_candidates(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
+                                   int* elems_per_thread, int cap, int* count) {
+  g_err.clear();
+  if (!p || !count || cap < 0 || (cap > 0 && (!lines || !elems_per_thread))) return fail(GPSOC_EINVAL, "bad arguments");
+  if (level < 0 || level > p->max_level || axis < 0 || axis >= p->dim) return fail(GPSOC_EINVAL, "bad level or axis");
+  if (precision != GPSOC_FP64 && precision != GPSOC_MIXED && precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
+  const Geo g = make_geo(p, level);
+  *count = (precision == GPSOC_FP64) ? tile_candidates<double>(g, axis, lines, elems_per_thread, cap)
+                                     : tile_candidates<float>(g, axis, lines, elems_per_thread, cap);
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_tuning_set(const gpsoc_problem* p, int level, int axis, int precision, int lines,
+                              int elems_per_thread) {
+  g_err.clear();
+  if (!p) return fail(GPSOC_EINVAL, "NULL problem");
+  if (level < 0 || level > p->max_level || axis < 0 || axis >= p->dim) return fail(GPSOC_EINVAL, "bad level or axis");
+  if (precision != GPSOC_FP64 && precision != GPSOC_MIXED && precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
+  if (lines < 0) return fail(GPSOC_EINVAL, "lines must be >= 0");
+  const Geo g = make_geo(p, level);
+  const bool ok = (precision == GPSOC_FP64) ? tile_set<double>(g, p->batch, axis, lines, elems_per_thread)
+                                            : tile_set<float>(g, p->batch, axis, lines, elems_per_thread);
+  if (!ok) return fail(GPSOC_EINVAL, "tile does not fit (see gpsoc_tile_candidates)");
+  gpsoc_problem* q = const_cast<gpsoc_problem*>(p);
+  for (int k = 0; k < 4; ++k)
+    if (q->graph[k]) { cudaGraphExecDestroy(q->graph[k]); q->graph[k] = nullptr; }   // captured with the old tiles
+  return GPSOC_OK;
+}
+
+gpsoc_status gpsoc_autotune(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int* lines, int* elems_per_thread) {
+  g_err.clear();
+  if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
+  if (!opts) return fail(GPSOC_EINVAL, "opts is NULL");
+  if (!p->has_state) return fail(GPSOC_ESTATE, "no initial guess set");
+  if (opts->precision != GPSOC_FP64 && opts->precision != GPSOC_MIXED && opts->precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
+  if (iters < 1) iters = 6;
+  const int prec = opts->precision;
+  const int level = p->level;
+  const Geo g = make_geo(p, level);
+  const size_t bytes = sizeof(double2) * (size_t)p->batch * 3 * g.npts;
+  // every candidate starts from the same state (kept in the FP64 scratch D)
+  CK(cudaMemcpyAsync(p->b64.D, p->b64.Phi, bytes, cudaMemcpyDeviceToDevice, p->stream));
+  std::vector<double> ms(128);
+  // average time per iteration of the passes whose tile the axis sets: the column passes
+  // of that axis, or (axis 0) every other pass (row tiles also set the elementwise blocks)
+  auto time_axis = [&](int axis, double* t) -> gpsoc_status {
+    CK(cudaMemcpyAsync(p->b64.Phi, p->b64.D, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    int nk = 0;
+    const gpsoc_status st = gpsoc_profile(p, opts, iters, ms.data(), (int)ms.size(), &nk);
+    if (st != GPSOC_OK) return st;
+    *t = 0.0;
+    for (int k = 0; k < nk && k < (int)ms.size(); ++k) {
+      const std::string& nm = p->prof_names[k];
+      const bool col = nm.compare(0, 3, "col") == 0;
+      const bool mine = (axis == 0) ? !col : nm.compare(0, 4, axis == 1 ? "coly" : "colz") == 0;
+      if (mine) *t += ms[k];
+    }
+    return GPSOC_OK;
+  };
+  gpsoc_status s = GPSOC_OK;
+  for (int axis = 0; axis < p->dim && s == GPSOC_OK; ++axis) {
+    int cl[64], ce[64];
+    const int nc = std::min(64, (prec == GPSOC_FP64) ? tile_candidates<double>(g, axis, cl, ce, 64)
+                                                     : tile_candidates<float>(g, axis, cl, ce, 64));
+    s = gpsoc_tuning_set(p, level, axis, prec, 0, 0);            // the rule first
+    double best = 0.0;
+    if (s == GPSOC_OK) s = time_axis(axis, &best);
+    int bl = 0, be = 0;
+    for (int c = 0; c < nc && s == GPSOC_OK; ++c) {
+      s = gpsoc_tuning_set(p, level, axis, prec, cl[c], ce[c]);
+      double t = 0.0;
+      if (s == GPSOC_OK) s = time_axis(axis, &t);
+      if (s == GPSOC_OK && t < best) { best = t; bl = cl[c]; be = ce[c]; }
+    }
+    if (s == GPSOC_OK) s = gpsoc_tuning_set(p, level, axis, prec, bl, be);
+  }
+  cudaMemcpyAsync(p->b64.Phi, p->b64.D, bytes, cudaMemcpyDeviceToDevice, p->stream);
+  if (s != GPSOC_OK) return s;
+  CK(cudaStreamSynchronize(p->stream));
+  for (int axis = 0; axis < 3; ++axis) {
+    int l = 0, e = 0, th = 0;
+    if (axis < p->dim) {
+      if (prec == GPSOC_FP64) tile_shape<double>(g, axis, p->batch, l, e, th);
+      else tile_shape<float>(g, axis, p->batch, l, e, th);
+    }
+    if (lines) lines[axis] = l;
+    if (elems_per_thread) elems_per_thread[axis] = e;
+  }
+  return GPSOC_OK;
+}
+
 gpsoc_status gpsoc_tile_shape(const gpsoc_problem* p, int level, int axis, int precision, int* lines,
                               int* elems_per_thread, int* threads) {
   g_err.clear();
   if (!p || !lines || !elems_per_thread || !threads) return fail(GPSOC_EINVAL, "NULL argument");
   if (level < 0 || level > p->max_level || axis < 0 || axis >= p->dim) return fail(GPSOC_EINVAL, "bad level or axis");
-  if (check_precision(precision) != GPSOC_OK) return GPSOC_EINVAL;
+  if (precision != GPSOC_FP64 && precision != GPSOC_MIXED && precision != GPSOC_HYBRID)
+    return fail(GPSOC_EINVAL, "unknown precision");
   const Geo g = make_geo(p, level);
-  if (precision == GPSOC_MIXED) tile_shape<float>(g, axis, p->batch, *lines, *elems_per_thread, *threads);
+  if (precision != GPSOC_FP64) tile_shape<float>(g, axis, p->batch, *lines, *elems_per_thread, *threads);
   else tile_shape<double>(g, axis, p->batch, *lines, *elems_per_thread, *threads);
   return GPSOC_OK;
 }

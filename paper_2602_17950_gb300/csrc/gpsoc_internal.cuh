@@ -121,6 +121,7 @@ struct OptsDev {
   double tol_rel;   // energy stop: |dE| < tol + tol_rel * |E|
   int precond;      // GPSOC_PRECOND_*
   double res32;     // FP32 phase: ends (or never starts) once max |r| < res32 (0 = no residual rule)
+  int line_search;  // 0: Algorithm 2's quadratic model; 1: the minimiser of Eq. theta
 };
 
 // reduction slots (per solve); partial sums live in part[(s * NSLOT + slot) * pmax + block]
@@ -465,5 +466,10 @@ cudaError_t chain_prepare();   // sets max dynamic shared memory attributes
 // FFT elements per thread and threads per block, for a launch over nsolve solves
 template <class T>
 void tile_shape(const Geo& g, int axis, int nsolve, int& lines, int& ept, int& threads);
+// tuned tiles: set (lines = 0 clears) and the list of valid candidates of an axis
+template <class T>
+bool tile_set(const Geo& g, int nsolve, int axis, int lines, int ept);
+template <class T>
+int tile_candidates(const Geo& g, int axis, int* lines, int* ept, int cap);
 
 }  // namespace gpsoc

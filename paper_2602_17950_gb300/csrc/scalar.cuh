@@ -229,6 +229,66 @@ __device__ __forceinline__ double energy_change(const SolveState& S, double c0, 
   return energy_change_sc(S, c0, c1, sn, cs, p_norm(S.P2));
 }
 
+// Eq. theta: theta_n = argmin_{theta > 0} E(cos t Phi + sin t P/|P|), on the explicit
+// sin/cos form of the energy change.  With u = -s^2, v = 2cs/|P|, w = s^2/|P|^2 the change
+// is a quadratic polynomial in (u, v, w) (energy_change_sc); its t-derivative follows with
+// du/dt = -sin 2t, dv/dt = 2 cos 2t/|P|, dw/dt = sin 2t/|P|^2.  The minimiser taken is the
+// first zero of the derivative found by doubling from the quadratic model's t0 (E has
+// period pi and decreases at 0+), solved by Newton steps kept inside the bracket
+// (bisection when a step leaves it).  If no sign change is met up to pi, t0 is kept.
+struct TrigForm {
+  double lu, l1, l2;                 // linear coefficients of u, v, w
+  double huu, hu1, hu2, h11, h12, h22;   // second derivatives of the change in (u, v, w)
+  double inv_nP, inv_nP2;
+  // derivative (g1) and second derivative (g2) of the energy change at t
+  __device__ __forceinline__ void eval(double t, double& g1, double& g2) const {
+    double s2, c2;
+    sincos(2.0 * t, &s2, &c2);
+    const double u = -0.5 * (1.0 - c2), v = s2 * inv_nP, w = 0.5 * (1.0 - c2) * inv_nP2;
+    const double du = -s2, dv = 2.0 * c2 * inv_nP, dw = s2 * inv_nP2;
+    const double ddu = -2.0 * c2, ddv = -4.0 * s2 * inv_nP, ddw = 2.0 * c2 * inv_nP2;
+    const double Au = lu + huu * u + hu1 * v + hu2 * w;
+    const double A1 = l1 + hu1 * u + h11 * v + h12 * w;
+    const double A2 = l2 + hu2 * u + h12 * v + h22 * w;
+    g1 = Au * du + A1 * dv + A2 * dw;
+    g2 = Au * ddu + A1 * ddv + A2 * ddw + huu * du * du + h11 * dv * dv + h22 * dw * dw +
+         2.0 * (hu1 * du * dv + hu2 * du * dw + h12 * dv * dw);
+  }
+};
+
+__device__ __forceinline__ double exact_theta(const SolveState& S, double c0, double c1, const PNorm& pn, double t0) {
+  TrigForm f;
+  const double* I = S.I;
+  const double* J = S.J;
+  const double QFP = S.HPhiP - c0 * I[1] - c1 * J[1];
+  f.lu = S.Q + c0 * I[0] + c1 * J[0];
+  f.l1 = QFP + c0 * I[1] + c1 * J[1];
+  f.l2 = S.HPP + c0 * I[2] + c1 * J[2];
+  f.huu = c0 * I[0] + c1 * J[0]; f.hu1 = c0 * I[1] + c1 * J[1]; f.hu2 = c0 * I[2] + c1 * J[2];
+  f.h11 = c0 * I[3] + c1 * J[3]; f.h12 = c0 * I[4] + c1 * J[4]; f.h22 = c0 * I[5] + c1 * J[5];
+  f.inv_nP = pn.inv_nP; f.inv_nP2 = pn.inv_nP2;
+  const double PI = 3.14159265358979323846;
+  double lo = 0.0, hi = fmin(t0, PI), g1, g2;
+  f.eval(hi, g1, g2);
+  while (g1 < 0.0 && hi < PI) {
+    lo = hi;
+    hi = fmin(2.0 * hi, PI);
+    f.eval(hi, g1, g2);
+  }
+  if (g1 < 0.0) return t0;
+  double t = hi;   // Newton from the right end of the bracket
+  for (int it = 0; it < 100; ++it) {
+    f.eval(t, g1, g2);
+    if (g1 == 0.0) break;
+    if (g1 < 0.0) lo = t; else hi = t;
+    double tn = (g2 > 0.0) ? t - g1 / g2 : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (fabs(tn - t) <= 1e-15 * t || hi - lo <= 2e-16 * hi) { t = tn; break; }
+    t = tn;
+  }
+  return t;
+}
+
 // gather the step-model sums of the P chain into S (thread 0 holds the result);
 // a_n, b_n of Eqs. an, bn
 __device__ __forceinline__ void step_sums(const ScalarCtx& X, int s, double* scratch, SolveState& S, PNorm& pn) {
@@ -294,6 +354,7 @@ __device__ __forceinline__ void step_decide(const ScalarCtx& X, int s, SolveStat
     return;
   }
   double theta = (a > 0.0 && b < 0.0) ? -b / (2.0 * a) : O.theta_trial;
+  if (O.line_search == 1) theta = exact_theta(S, ph.c0, ph.c1, pn, theta);
   bool accepted = false;
   double dE = 0.0, sn = 0.0, cs = 1.0;
   for (int h = 0; h <= O.max_halvings; ++h) {

@@ -52,7 +52,7 @@ class Opts(C.Structure):
                 ("max_halvings", C.c_int), ("cm_levels", C.c_int), ("check_every", C.c_int),
                 ("fp32_switch", C.c_double), ("fp32_min_points", C.c_int), ("precond", C.c_int),
                 ("fp32_res_switch", C.c_double), ("fp32_carry", C.c_int), ("hybrid_refresh", C.c_int),
-                ("hybrid_lead_res", C.c_double)]
+                ("hybrid_lead_res", C.c_double), ("line_search", C.c_int)]
 
 
 class Result(C.Structure):
@@ -102,6 +102,10 @@ _PROTOS = {
     "gpsoc_kernel_launches": (C.c_uint64, [C.c_void_p]),
     "gpsoc_tile_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int)]),
+    "gpsoc_tile_candidates": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                        C.POINTER(C.c_int)]),
+    "gpsoc_tuning_set": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "gpsoc_autotune": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.c_int, C.c_void_p, C.c_void_p]),
     "gpsoc_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gpsoc_apply_h_noalloc": (C.c_int, [C.POINTER(Grid), C.POINTER(Trap), C.POINTER(Params), C.c_int, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -238,11 +242,12 @@ class Problem:
     def opts(precision=GPSOC_FP64, stop=GPSOC_STOP_ENERGY, tol=1e-12, res_tol=0.0, max_iter=100000,
              theta_trial=0.0, sigma=0.0, max_halvings=0, cm_levels=1, check_every=0, fp32_switch=0.0,
              fp32_min_points=0, precond="combined", fp32_res_switch=0.0, fp32_carry=0, hybrid_refresh=0,
-             hybrid_lead_res=0.0):
+             hybrid_lead_res=0.0, line_search=0):
         pk = PRECONDS.index(precond) if isinstance(precond, str) else int(precond)
         return Opts(precision, stop, tol, res_tol, max_iter, theta_trial, sigma, max_halvings, cm_levels,
                     check_every, fp32_switch, fp32_min_points, pk, fp32_res_switch, int(fp32_carry),
-                    int(hybrid_refresh), float(hybrid_lead_res))
+                    int(hybrid_refresh), float(hybrid_lead_res),
+                    1 if line_search in (1, "exact") else 0)
 
     # -------------------------------------------------------------- state
     def set_initial(self, psi: np.ndarray, level=0):
@@ -329,6 +334,29 @@ class Problem:
 
     def kernel_launches(self) -> int:
         return int(library().gpsoc_kernel_launches(self._h))
+
+    def tile_candidates(self, axis, level=0, precision=GPSOC_FP64):
+        """Valid (lines per tile, FFT elements per thread) pairs of the passes along `axis`."""
+        cnt = C.c_int(0)
+        _check(library().gpsoc_tile_candidates(self._h, int(level), int(axis), int(precision), None, None, 0,
+                                               C.byref(cnt)))
+        la = np.zeros(max(cnt.value, 1), dtype=np.int32)
+        ea = np.zeros(max(cnt.value, 1), dtype=np.int32)
+        _check(library().gpsoc_tile_candidates(self._h, int(level), int(axis), int(precision), _ptr(la), _ptr(ea),
+                                               cnt.value, C.byref(cnt)))
+        return list(zip(la[:cnt.value].tolist(), ea[:cnt.value].tolist()))
+
+    def tuning_set(self, axis, lines, ept, level=0, precision=GPSOC_FP64):
+        """Use this tile (lines = 0: the built-in rule) for every problem of this grid, batch, precision."""
+        _check(library().gpsoc_tuning_set(self._h, int(level), int(axis), int(precision), int(lines), int(ept)))
+
+    def autotune(self, iters=6, **kw):
+        """Time every candidate tile of each axis on the current level; returns [(lines, ept)] per axis."""
+        o = self.opts(**kw)
+        la = np.zeros(3, dtype=np.int32)
+        ea = np.zeros(3, dtype=np.int32)
+        _check(library().gpsoc_autotune(self._h, C.byref(o), int(iters), _ptr(la), _ptr(ea)))
+        return [(int(la[a]), int(ea[a])) for a in range(self.dim)]
 
     def tile_shape(self, axis, level=0, precision=GPSOC_FP64):
         """(lines per tile, FFT elements per thread, threads) of the passes along `axis`."""

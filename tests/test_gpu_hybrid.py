@@ -100,7 +100,8 @@ def test_hybrid_served_results_equal_solving_alone():
     trap = {"kind": 0, "g": (1.0, 1.1, 1.2)}
     reqs = [((32, 32), (6.0, 6.0), (0.3, 0.5, 60.0, -1.0)), ((64, 64), (8.0, 8.0), (0.5, 0.8, 100.0, 2.0)),
             ((16, 16, 16), (5.0, 5.0, 5.0), (0.2, 0.4, 30.0, -2.0)), ((32, 32), (6.0, 6.0), (0.0, 1.2, 20.0, 0.0))]
-    opts = dict(tol=1e-12, res_tol=2e-10)   # as the other served-form test: soft modes need a tight residual
+    # mu moves to first order with the state: requests with soft modes need a tight residual
+    opts = dict(tol=1e-13, res_tol=5e-11)
     guesses = [si.gaussian_guess(n, L, 410 + k, vortex=(len(n) == 2)) for k, (n, L, _) in enumerate(reqs)]
     done = {}
     with Server(hbm_budget_bytes=8e9, slots_per_bucket=4, precision=HYBRID, iters_per_step=16) as sv:
@@ -116,7 +117,7 @@ def test_hybrid_served_results_equal_solving_alone():
             ra = p.solve(**opts)[0]
             pa = p.psi()[0]
         assert r["status"] == "OK" and ra["status"] == "OK", (k, r, ra)
-        assert r["res_inf"] < 2e-10
+        assert r["res_inf"] < 5e-11
         assert r["energy"] == pytest.approx(ra["energy"], rel=1e-10)
         assert r["mu"] == pytest.approx(ra["mu"], rel=1e-10)
         assert np.max(np.abs(np.abs(psi) ** 2 - np.abs(pa) ** 2)) < 1e-8
