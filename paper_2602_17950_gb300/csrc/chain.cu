@@ -200,38 +200,26 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
           buf0[c * CP + pos] = p;
         }
       } else if (MODE == ROW_FWD_PRE_HY) {
-        // GPSOC_HYBRID: H Phi = H_lin Phi + c0 rho Phi + c1 (F.f) Phi and r = H Phi - mu Phi in
-        // FP64 from the FP64 state (the residual keeps FP64 accuracy), stored as FP32; the
-        // preconditioner's transforms then run on P_V^{1/2} r in FP32
+        // GPSOC_HYBRID: r = H Phi - mu Phi in FP64 from the FP64 state and H(Phi) (the residual
+        // keeps FP64 accuracy), stored as FP32; the preconditioner's transforms then run on
+        // P_V^{1/2} r in FP32
         const int pk = A.sc.opts.precond;
         const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
-        double2 f[3], hl[3];
-        double m[3], rho = 0.0;
+        const double mu64 = S.mu;
+        double2 f[3];
+        double rho = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           f[c] = A.phi64[sbase + c * npts + off];
-          hl[c] = A.hl64[sbase + c * npts + off];
-          m[c] = f[c].x * f[c].x + f[c].y * f[c].y;
-          rho += m[c];
+          rho += f[c].x * f[c].x + f[c].y * f[c].y;
         }
-        double ax, ay;
-        spin_a<double>(f[0], f[1], f[2], ax, ay);
-        const double Fz = m[0] - m[2];
-        double fr[3], fi[3];
-        fr[0] = Fz * f[0].x + (ax * f[1].x - ay * f[1].y);
-        fi[0] = Fz * f[0].y + (ax * f[1].y + ay * f[1].x);
-        fr[1] = (ax * f[0].x + ay * f[0].y) + (ax * f[2].x - ay * f[2].y);
-        fi[1] = (ax * f[0].y - ay * f[0].x) + (ax * f[2].y + ay * f[2].x);
-        fr[2] = (ax * f[1].x + ay * f[1].y) - Fz * f[2].x;
-        fi[2] = (ax * f[1].y - ay * f[1].x) - Fz * f[2].y;
-        const double mu64 = S.mu, c0d = ph.c0, c1d = ph.c1;
         const long long row = off / nx;
         const W V = trap_value<W>(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
         const W rhow = (W)rho;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double rr = hl[c].x + c0d * rho * f[c].x + c1d * fr[c] - mu64 * f[c].x;
-          const double ri = hl[c].y + c0d * rho * f[c].y + c1d * fi[c] - mu64 * f[c].y;
+          const double2 h = A.hl64[sbase + c * npts + off];
+          const double rr = h.x - mu64 * f[c].x, ri = h.y - mu64 * f[c].y;
           const C rc = mk<C>(rr, ri);
           A.out1[sbase + c * npts + off] = rc;
           acc[0] = fmax(acc[0], (W)sqrt((W)(rr * rr + ri * ri)));

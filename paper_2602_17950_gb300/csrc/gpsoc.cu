@@ -571,6 +571,7 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
   h.p = p->b32.P[(parity & 1) ^ 1];   // direction of the previous iteration
   h.hlp = p->b32.HPhi;                // its H_lin P
   h.phi32 = p->b32.Phi;
+  h.hphi = p->b64.Z;                  // H(Phi): the FP64 Z buffer is free in hybrid iterations
   h.npts = g.npts;
   h.bps = row_blocks_per_solve<float>(g, p->batch);   // the fused tail reads FP32 tile counts
   h.nsolve = p->batch;
@@ -641,7 +642,7 @@ gpsoc_status enqueue_iteration_hy(gpsoc_problem* p, int level, int parity, const
   // r in FP64 (stored FP32), stopping test, P_C r in FP32, beta
   ChainArgs<float> f = a;
   f.fuse = 1;
-  f.phi64 = D.Phi; f.hl64 = D.HPhi; f.out0 = F.A; f.out1 = F.R[cur];
+  f.phi64 = D.Phi; f.hl64 = D.Z; f.out0 = F.A; f.out1 = F.R[cur];
   RL<float>(p, ROW_FWD_PRE_HY, f);
   ChainArgs<float> m = a;
   m.fuse = 0;
@@ -726,7 +727,7 @@ gpsoc_status hy_verify(gpsoc_problem* p, int level, const OptsDev& o, int* resum
   f.gate = GATE_ALL;
   f.sc = sc;
   f.fuse = 1;
-  f.phi64 = p->b64.Phi; f.hl64 = p->b64.HPhi; f.out0 = p->b32.A; f.out1 = p->b32.R[0];
+  f.phi64 = p->b64.Phi; f.hl64 = p->b64.Z; f.out0 = p->b32.A; f.out1 = p->b32.R[0];
   RL<float>(p, ROW_FWD_PRE_HY, f);
   CK(cudaGetLastError());
   s = sync_state(p);

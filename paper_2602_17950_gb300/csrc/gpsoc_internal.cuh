@@ -184,7 +184,7 @@ struct ChainArgs {
   ScalarCtx sc;
   // GPSOC_HYBRID passes of an FP32 chain that also read the FP64 state
   const double2* phi64;   // Phi (FP64)
-  const double2* hl64;    // H_lin Phi (FP64)
+  const double2* hl64;    // H(Phi) (FP64), for ROW_FWD_PRE_HY
   // GPSOC_HYBRID, last column pass of the P chain: the spectrum of Phi (advanced by the
   // step applied this iteration when khat_upd is set) and of the previous P, both updated
   // in place, for the exact per-component kinetic sums of alpha
@@ -436,8 +436,8 @@ enum RowMode {
   ROW_INV_PLAIN,       // out0 = scale * F_x^-1(in0)
   ROW_INV_LIN,         // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
   ROW_FWD_UPD,         // Phi (in0, written back to out1) <- pending step with P (in2); out0 = F_x(Phi)
-  ROW_FWD_PRE_HY,      // FP32 pass of GPSOC_HYBRID: r = H_lin Phi + nonlinear(Phi) - mu Phi in FP64 from
-                       // phi64, hl64 -> out1 (FP32); out0 = F_x(P_V^{1/2} r); reduce max|r| in FP64
+  ROW_FWD_PRE_HY,      // FP32 pass of GPSOC_HYBRID: r = H Phi - mu Phi in FP64 from phi64 and H(Phi)
+                       // (hl64) -> out1 (FP32); out0 = F_x(P_V^{1/2} r); reduce max|r|
   ROW_INV_P_HY         // FP32 pass of GPSOC_HYBRID: as ROW_INV_P with in4 = r (slot HPHIP = Re<r, P>),
                        // out0 = H_lin P, and Re<P, Phi> summed in FP64 against phi64
 };

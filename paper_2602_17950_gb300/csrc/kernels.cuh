@@ -74,6 +74,7 @@ struct HyArgs {
   const float2* p;       // the pending direction P (FP32)
   const float2* hlp;     // H_lin P (FP32)
   float2* phi32;         // FP32 copy of Phi for the FP32 passes
+  double2* hphi;         // H(Phi) = H_lin Phi + nonlinear terms (FP64), written by HY_REDUCE
   long long npts;
   int bps, nsolve, gate, flags;
   int fuse;

@@ -176,7 +176,10 @@ __global__ void k_elem(ElemArgs<T> A) {
 }
 
 // GPSOC_HYBRID opening pass (see HyArgs).  Same block decomposition as the row
-// passes; all arithmetic on the state in FP64.
+// passes.  The state, H_lin Phi, H(Phi) and the sums that set the energy, mu and the
+// normalisation (<H_lin Phi, Phi>, rho^2, |F|^2, masses) are FP64; the alpha_l pieces
+// V |phi_l|^2 and rho |phi_l|^2, which only shift the preconditioner, are summed from
+// FP32 products in double-float.
 __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
   __shared__ double scratch[16 * 8 + 16];
   __shared__ int last_flag;
@@ -190,12 +193,15 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
   const bool upd = (A.flags & HY_UPD) && S.pending;
   const bool rec = upd && (A.flags & HY_REC);
   const bool red = (A.flags & HY_REDUCE) != 0;
-  const double uc = S.upd_c, us = S.upd_s, usc = S.upd_scale;
+  // Phi' = g (c Phi + t P): with uc = g c, ut = g t, and the change Phi' - Phi = (uc - 1) Phi + ut P
+  const double uc = S.upd_scale * S.upd_c, ut = S.upd_scale * S.upd_s, ucm1 = uc - 1.0;
   const PhysDev ph = A.phys[s];
+  const double c0 = ph.c0, c1 = ph.c1;
   const int nx = A.g.n[0], ny = A.g.n[1];
-  double acc[12];
+  double acc[6];
+  float acc32[6];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 6; ++k) { acc[k] = 0.0; acc32[k] = 0.0f; }
   double dmax = 0.0;
   for (long long e = threadIdx.x; e < per; e += blockDim.x) {
     const long long off = ebase + e;
@@ -204,30 +210,27 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
     for (int c = 0; c < 3; ++c) {
       const long long i = sbase + c * npts + off;
       f[c] = A.phi[i];
-      if (red) hl[c] = A.hl[i];
+      if (red && !rec) hl[c] = A.hl[i];
       if (upd) {
         // the accepted step (Eqs. formula-pcg, update) with the exact tangent direction
         const float2 q = A.p[i];
-        const double2 o = make_double2(usc * (uc * f[c].x + us * (double)q.x), usc * (uc * f[c].y + us * (double)q.y));
-        const double dr = o.x - f[c].x, di = o.y - f[c].y;
+        const double qx = (double)q.x, qy = (double)q.y;
+        const double dr = ucm1 * f[c].x + ut * qx, di = ucm1 * f[c].y + ut * qy;
         dmax = fmax(dmax, dr * dr + di * di);
-        A.phi[i] = o;
-        f[c] = o;
+        f[c] = make_double2(f[c].x + dr, f[c].y + di);
+        A.phi[i] = f[c];
         if (rec) {
-          // H_lin is linear: H_lin Phi' = s (c H_lin Phi + t H_lin P)
+          // H_lin is linear: H_lin Phi' = g (c H_lin Phi + t H_lin P)
           const double2 h0 = A.hl[i];
           const float2 hq = A.hlp[i];
-          const double2 h1 = make_double2(usc * (uc * h0.x + us * (double)hq.x), usc * (uc * h0.y + us * (double)hq.y));
-          A.hl[i] = h1;
-          hl[c] = h1;
+          hl[c] = make_double2(uc * h0.x + ut * (double)hq.x, uc * h0.y + ut * (double)hq.y);
+          A.hl[i] = hl[c];
         }
       }
     }
     if (!red) continue;
-    // energy pieces of Eq. energy with H_lin Phi given: <H_lin Phi, Phi>, rho^2, |F|^2, and
-    // the alpha_l pieces V |phi_l|^2, rho |phi_l|^2 (Eq. PreCnstAlpha), masses
-    const long long row = off / nx;
-    const double V = trap_value<double>(A.trap, A.g, (int)(off - row * nx), (int)(row % ny), (int)(row / ny), off);
+    // H(Phi) = H_lin Phi + c0 rho Phi + c1 (F.f) Phi (Eqs. eigen1-eigen3) and the sums of the
+    // energy (Eq. energy) and of alpha_l (Eq. PreCnstAlpha)
     double m[3], rho = 0.0, q = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -239,14 +242,32 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
     const double ar = f[1].x * f[0].x + f[1].y * f[0].y + f[2].x * f[1].x + f[2].y * f[1].y;
     const double ai = f[1].x * f[0].y - f[1].y * f[0].x + f[2].x * f[1].y - f[2].y * f[1].x;
     const double Fz = m[0] - m[2];
+    double fr[3], fi[3];
+    fr[0] = Fz * f[0].x + (ar * f[1].x - ai * f[1].y);
+    fi[0] = Fz * f[0].y + (ar * f[1].y + ai * f[1].x);
+    fr[1] = (ar * f[0].x + ai * f[0].y) + (ar * f[2].x - ai * f[2].y);
+    fi[1] = (ar * f[0].y - ai * f[0].x) + (ar * f[2].y + ai * f[2].x);
+    fr[2] = (ar * f[1].x + ai * f[1].y) - Fz * f[2].x;
+    fi[2] = (ar * f[1].y - ai * f[1].x) - Fz * f[2].y;
+    const double c0r = c0 * rho;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      A.hphi[sbase + c * npts + off] =
+          make_double2(hl[c].x + c0r * f[c].x + c1 * fr[c], hl[c].y + c0r * f[c].y + c1 * fi[c]);
     acc[0] += q;
     acc[1] += rho * rho;
     acc[2] += 2.0 * (ar * ar + ai * ai) + Fz * Fz;
+    acc[3] += m[0];
+    acc[4] += m[1];
+    acc[5] += m[2];
+    const long long row = off / nx;
+    const float V = trap_value<float>(A.trap, A.g, (int)(off - row * nx), (int)(row % ny), (int)(row / ny), off);
+    const float rf = (float)rho;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      acc[3 + c] += V * m[c];
-      acc[6 + c] += rho * m[c];
-      acc[9 + c] += m[c];
+      const float mf = (float)m[c];
+      acc32[c] += V * mf;
+      acc32[3 + c] += rf * mf;
     }
   }
   double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
@@ -257,12 +278,18 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
     if (threadIdx.x == 0) P[(long long)SL_DPHIINF * A.pmax] = v1[0];
   }
   if (!red) return;
-  const bool mx[12] = {};
-  block_reduce<12>(acc, scratch, mx);
+  const bool mx[6] = {};
+  block_reduce<6>(acc, scratch, mx);
+  double v32[6];
+  block_reduce_df<6>(acc32, v32, scratch);
   if (threadIdx.x == 0) {
-    const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2, SL_M0, SL_M1, SL_M2};
+    const int slots[6] = {SL_Q, SL_RHO2, SL_F2, SL_M0, SL_M1, SL_M2};
+    const int slots32[6] = {SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2};
 #pragma unroll
-    for (int k = 0; k < 12; ++k) P[(long long)slots[k] * A.pmax] = acc[k];
+    for (int k = 0; k < 6; ++k) {
+      P[(long long)slots[k] * A.pmax] = acc[k];
+      P[(long long)slots32[k] * A.pmax] = v32[k];
+    }
   }
   if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, scratch);
 }
