@@ -127,16 +127,17 @@ def fft_flops(n: int) -> float:
 KERNEL_WORK = {
     "row_fwd_upd": (1, "row", 4), "row_fwd": (1, "row", 2), "coly_ymid_h": (3, "col", 3),
     "row_inv_h": (2, "row", 4), "row_fwd_pre": (1, "row", 4), "coly_mid_pre": (2, "col", 2),
-    "row_inv_pre": (1, "row", 5), "el_dir": (0, "row", 4), "row_fwd_proj": (1, "row", 5),
+    "row_inv_pre": (1, "row", 6), "row_fwd_proj": (1, "row", 5),
     "row_inv_p": (2, "row", 5),
 }
 # Hybrid iteration (FP64 state, FP32 directions): algorithmic bytes per grid point and
 # component of each pass (FP64 complex 16 B, FP32 complex 8 B; every array read or
 # written once).  hy_upd: R Phi, H_lin Phi (FP64), P, H_lin P (FP32); W Phi, H_lin Phi,
-# FP32 Phi.  row_fwd_pre_hy: R Phi, H_lin Phi; W r, F_x(P_V^1/2 r).  coly_ymid_h in the
-# hybrid P chain also reads and writes the spectra of Phi and P.  row_inv_p_hy: R T', G,
-# P, FP32 Phi, r, FP64 Phi; W H_lin P.
-HYBRID_BYTES = {"hy_upd": 88, "row_fwd_pre_hy": 48, "coly_mid_pre": 16, "row_inv_pre": 40, "el_dir": 32,
+# H(Phi) (FP64), FP32 Phi.  row_fwd_pre_hy: R Phi, H(Phi); W r, F_x(P_V^1/2 r).
+# row_inv_pre: R spectrum, FP32 Phi, r, r_prev, P_prev; W z.  coly_ymid_h in the hybrid P
+# chain also reads and writes the spectra of Phi and P.  row_inv_p_hy: R T', G, P, FP32
+# Phi, r, FP64 Phi; W H_lin P.
+HYBRID_BYTES = {"hy_upd": 104, "row_fwd_pre_hy": 48, "coly_mid_pre": 16, "row_inv_pre": 48,
                 "row_fwd_proj": 40, "coly_ymid_h": 56, "row_inv_p_hy": 64}
 
 
@@ -732,10 +733,23 @@ def kernel_case(args):
         p.set_initial(psi)
         p.profile(iters=args.warmup, precision=prec, tol=TOL)
         prof = p.profile(iters=max(args.steps, 1) * 10, precision=prec, tol=TOL)
-    elem = 8 if prec == 1 else 16
+        # the same iterations as the solver runs them (graph replays, periodic checks and
+        # exact recomputations), from the same start, without the FP64 lead-in
+        kw = dict(tol=1e-300, res_tol=0.0, cm_levels=1, precision=prec, hybrid_lead_res=-1.0, raise_on_error=False)
+        solve_iters = 200 * max(args.steps, 1)
+        p.set_initial(psi)
+        p.solve(max_iter=32, **kw)
+        p.set_initial(psi)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = p.solve(max_iter=solve_iters, **kw)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        its = max(int(sum(x["iters"] for x in r)) // args.batch, 1)
     out = {"kernel_case": f"{n[0]}x{n[1]} x {args.batch} solves", "precision": args.precision,
            "us_per_launch": {k: round(v * 1e3, 2) for k, v in prof},
            "iteration_us": round(sum(v for _, v in prof) * 1e3, 2),
+           "solver_iteration_us": round(t_solve / its * 1e6, 2), "solver_iterations": its,
            "gbs_per_launch": {k: round(launch_bytes(k, n, prec) * args.batch / (v * 1e-3) / 1e9, 1)
                               for k, v in prof if launch_bytes(k, n, prec) > 0}}
     torch.cuda.synchronize()

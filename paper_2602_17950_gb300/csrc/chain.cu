@@ -303,8 +303,9 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
     return;
   }
   if (MODE == ROW_INV_PRE) {
-    // z = P_V^{1/2} F^-1[...] (Eq. PreCondMix); reduce Re<r, z>, Re<r_prev, z>
-    W acc[2] = {(W)0, (W)0};
+    // z = P_V^{1/2} F^-1[...] (Eq. PreCondMix); reduce Re<r, z>, Re<r_prev, z> (beta) and
+    // Re<z, Phi>, Re<P_prev, Phi>, Re<r, P_prev> (the direction's projection and slope)
+    W acc[5] = {(W)0, (W)0, (W)0, (W)0, (W)0};
     const bool use_prev = (A.in3 != nullptr) && !S.first;
     const int pk = A.sc.opts.precond;
     const bool use_pv = (pk == GPSOC_PRECOND_COMBINED || pk == GPSOC_PRECOND_POTENTIAL);
@@ -315,10 +316,11 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
       const int pos = r * NP + fft_pad<C>(j);
       const long long off = rbase + e;
       W rho = (W)0;
+      C f[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const C f = A.in1[sbase + c * npts + off];
-        rho += f.x * f.x + f.y * f.y;
+        f[c] = A.in1[sbase + c * npts + off];
+        rho += f[c].x * f[c].x + f[c].y * f[c].y;
       }
       const long long row = off / nx;
       const W V = trap_value<W>(A.trap, A.g, j, (int)(row % ny), (int)(row / ny), off);
@@ -332,15 +334,19 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
         A.out0[sbase + c * npts + off] = z;
         const C rr = A.in2[sbase + c * npts + off];
         acc[0] += rr.x * z.x + rr.y * z.y;
+        acc[2] += z.x * f[c].x + z.y * f[c].y;
         if (use_prev) {
           const C rp = A.in3[sbase + c * npts + off];
+          const C pp = A.in4[sbase + c * npts + off];
           acc[1] += rp.x * z.x + rp.y * z.y;
+          acc[3] += pp.x * f[c].x + pp.y * f[c].y;
+          acc[4] += rr.x * pp.x + rr.y * pp.y;
         }
       }
     }
-    const bool mx[2] = {false, false};
-    const int slots[2] = {SL_RZ, SL_RPZ};
-    store_partials<2, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
+    const bool mx[5] = {false, false, false, false, false};
+    const int slots[5] = {SL_RZ, SL_RPZ, SL_ZPHI, SL_PPHI, SL_RP};
+    store_partials<5, W>(acc, slots, mx, red, A.part, sslot, A.pmax, rb);
     if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_beta(A.sc, s, red);
     return;
   }

@@ -84,12 +84,12 @@ const char* col_name(int m, int axis) {
   return (m >= 0 && m < 7) ? n[axis == 2 ? 1 : 0][m] : "col_?";
 }
 const char* scalar_name(int ph) {
-  static const char* n[] = {"sc_init", "sc_obs", "sc_res", "sc_beta", "sc_cproj", "sc_step", "sc_clear",
-                            "sc_norm", "sc_model"};
+  static const char* n[] = {"sc_init", "sc_obs", "sc_res", "sc_beta", "sc_step", "sc_clear",
+                            "sc_norm", "sc_model", "sc_kin"};
   return (ph >= 0 && ph < (int)(sizeof(n) / sizeof(n[0]))) ? n[ph] : "sc_?";
 }
 const char* elem_name(int m) {
-  static const char* n[] = {"el_dir", "el_update", "el_mass", "el_scale"};
+  static const char* n[] = {"el_update", "el_mass", "el_scale"};
   return (m >= 0 && m < (int)(sizeof(n) / sizeof(n[0]))) ? n[m] : "el_?";
 }
 }  // namespace
@@ -109,6 +109,7 @@ struct gpsoc_problem {
   SolveState* h_st = nullptr;   // pinned mirror
   double* d_part = nullptr;
   int pmax = 0;
+  int nsm = 1;                  // SMs of the device (grid of the elementwise hybrid pass)
   unsigned* d_cnt = nullptr;    // per-solve block arrival counters of the fused scalar steps
   double* d_scale = nullptr;    // per-solve scale factors
   double* d_tmp = nullptr;      // 3*batch doubles + model outputs
@@ -363,10 +364,11 @@ void run_h_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, cx_t<T>* src, cx_
   RL<T>(p, ROW_INV_H, g);
 }
 
-// preconditioner chain: r = in0 - mu Phi (or in0 given as r) -> rout, z = P_C r -> zout
+// preconditioner chain: r = in0 - mu Phi (or in0 given as r) -> rout, z = P_C r -> zout; with
+// rprev and pprev the last pass also takes beta, the projection and Algorithm 2 Step 2
 template <class T>
 void run_pre_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* hphi, const cx_t<T>* phi,
-                   cx_t<T>* rout, const cx_t<T>* rprev, cx_t<T>* zout, int fuse) {
+                   cx_t<T>* rout, const cx_t<T>* rprev, cx_t<T>* zout, int fuse, const cx_t<T>* pprev = nullptr) {
   ChainArgs<T> f = a;
   f.fuse = fuse;
   f.in0 = hphi; f.in1 = phi; f.out0 = B.A; f.out1 = rout;
@@ -387,7 +389,7 @@ void run_pre_chain(gpsoc_problem* p, ChainArgs<T> a, Bufs<T>& B, const cx_t<T>* 
   ChainArgs<T> iv = a;
   iv.fuse = fuse;
   iv.given_r = 0;
-  iv.in0 = B.A; iv.in1 = phi; iv.in2 = rout; iv.in3 = rprev; iv.out0 = zout;
+  iv.in0 = B.A; iv.in1 = phi; iv.in2 = rout; iv.in3 = rprev; iv.in4 = pprev; iv.out0 = zout;
   RL<T>(p, ROW_INV_PRE, iv);
 }
 
@@ -420,15 +422,8 @@ gpsoc_status enqueue_iteration(gpsoc_problem* p, int level, Bufs<T>& B, int pari
   a.sc = scalar_ctx<T>(p, g, o, (fp32 ? 2 : 0) | (cur << 2));
   // apply the pending step, H(Phi^n), E, mu, alpha
   run_h_chain<T>(p, a, B, B.Phi, B.HPhi, B.P[prv], 1);
-  // r^n, stopping test, P_C r^n, beta
-  run_pre_chain<T>(p, a, B, B.HPhi, B.Phi, B.R[cur], B.R[prv], B.Z, 1);
-  // Re<D, Phi> and the beta = 0 decision
-  ElemArgs<T> e = elem_args<T>(p, g, GATE_ACTIVE);
-  e.in0 = B.Z; e.in1 = B.P[prv]; e.in2 = B.Phi; e.in3 = B.HPhi;
-  e.fuse = 1;
-  e.cnt = p->d_cnt;
-  e.sc = a.sc;
-  EL<T>(p, EL_DIR, e);
+  // r^n, stopping test, P_C r^n, beta, Re<D, Phi> and the beta = 0 decision
+  run_pre_chain<T>(p, a, B, B.HPhi, B.Phi, B.R[cur], B.R[prv], B.Z, 1, B.P[prv]);
   // P^n, step model, Algorithm 2
   run_p_chain<T>(p, a, B, B.Z, B.P[prv], B.Phi, B.HPhi, B.P[cur], 1);
   CK(cudaGetLastError());
@@ -573,13 +568,14 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
   h.phi32 = p->b32.Phi;
   h.hphi = p->b64.Z;                  // H(Phi): the FP64 Z buffer is free in hybrid iterations
   h.npts = g.npts;
-  h.bps = row_blocks_per_solve<float>(g, p->batch);   // the fused tail reads FP32 tile counts
+  h.bps = hy_blocks_per_solve(g, p->batch, p->nsm);
   h.nsolve = p->batch;
   h.gate = gate;
   h.flags = flags;
   h.fuse = (flags & HY_REDUCE) ? 1 : 0;
   h.cnt = p->d_cnt;
   h.sc = sc;
+  h.sc.nb_row = h.bps;                // its fused tail sums the partials this pass wrote
   return h;
 }
 
@@ -657,15 +653,8 @@ gpsoc_status enqueue_iteration_hy(gpsoc_problem* p, int level, int parity, const
   }
   ChainArgs<float> iv = a;
   iv.fuse = 1;
-  iv.in0 = F.A; iv.in1 = F.Phi; iv.in2 = F.R[cur]; iv.in3 = F.R[prv]; iv.out0 = F.Z;
-  RL<float>(p, ROW_INV_PRE, iv);
-  // Re<D, Phi>, the slope Re<r, D> and the beta = 0 decision
-  ElemArgs<float> e = elem_args<float>(p, g, GATE_ACTIVE);
-  e.in0 = F.Z; e.in1 = F.P[prv]; e.in2 = F.Phi; e.in3 = F.R[cur];
-  e.fuse = 1;
-  e.cnt = p->d_cnt;
-  e.sc = a.sc;
-  EL<float>(p, EL_DIR, e);
+  iv.in0 = F.A; iv.in1 = F.Phi; iv.in2 = F.R[cur]; iv.in3 = F.R[prv]; iv.in4 = F.P[prv]; iv.out0 = F.Z;
+  RL<float>(p, ROW_INV_PRE, iv);   // also beta, Re<D, Phi>, the slope Re<r, D> and Step 2
   // P, H_lin P (kept), step model with Re<r, P> and the FP64 radial part, Algorithm 2
   ChainArgs<float> pf = a;
   pf.fuse = 0;
@@ -1136,6 +1125,14 @@ gpsoc_status gpsoc_create(const gpsoc_grid* grid, const gpsoc_trap* trap, const 
   // the most blocks any pass can use per solve: one row, or one column line, per block
   p->pmax = (int)(g.npts / g.n[0]);
   for (int ax = 1; ax < p->dim; ++ax) p->pmax = std::max(p->pmax, (int)(g.npts / g.n[ax]));
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return bail(GPSOC_ECUDA, "device query failed");
+  }
+  // the elementwise hybrid pass: its block count grows with the points per level
+  p->pmax = std::max(p->pmax, hy_blocks_per_solve(g, batch, p->nsm));
   if (cudaMalloc(&p->d_part, sizeof(double) * (size_t)batch * NSLOT * p->pmax) != cudaSuccess)
     return bail(GPSOC_ENOMEM, "device allocation failed");
   if (cudaMalloc(&p->d_st, sizeof(SolveState) * batch) != cudaSuccess) return bail(GPSOC_ENOMEM, "device allocation failed");

@@ -132,14 +132,13 @@ enum Slot {
   SL_M0, SL_M1, SL_M2,                            // masses
   SL_RINF,                                        // max |r|
   SL_RZ, SL_RPZ,                                  // Re<r, z>, Re<r_prev, z>
-  SL_DPHI,                                        // Re<D, Phi>
   SL_P2,                                          // ||P||^2
   SL_HPP, SL_HPHIP, SL_RPHI,                      // <H_lin P,P>, Re<H Phi, P>, Re<P, Phi>
   SL_IFR, SL_IFP, SL_IRR, SL_IRP, SL_IPP,         // rho cross integrals
   SL_JFR, SL_JFP, SL_JRR, SL_JRP, SL_JPP,         // spin cross integrals
   SL_DPHIINF,                                     // max |Phi_new - Phi|^2
   SL_NORM,                                        // sum |phi|^2 for normalisation
-  SL_HD, SL_ZPHI, SL_HZ,                          // Re<H Phi, D>, Re<z, Phi>, Re<H Phi, z>
+  SL_ZPHI, SL_PPHI, SL_RP,                        // Re<z, Phi>, Re<P_prev, Phi>, Re<r, P_prev>
   SL_KPHI0, SL_KPHI1, SL_KPHI2,                   // GPSOC_HYBRID: sum 1/2 |k|^2 |Phi_hat_l|^2
   SL_KX0, SL_KX1, SL_KX2,                         //   and sum 1/2 |k|^2 Re(Phi_hat_l conj P_hat_l)
   NSLOT
@@ -432,7 +431,8 @@ enum RowMode {
   ROW_FWD_PRE,         // r = in0 - mu in1 -> out1; out0 = F_x(s * r); reduce max|r|
   ROW_INV_H,           // out0 = H(Phi) from T' (in0), G (in1), Phi (in2); energy reductions
   ROW_INV_P,           // reductions of the step model from T' (in0), G (in1), P (in2), Phi (in3), HPhi (in4)
-  ROW_INV_PRE,         // z = s * F_x^-1(in0)/npts -> out0; reduce <r,z>, <r_prev,z> (in2 = r, in3 = r_prev, in1 = Phi)
+  ROW_INV_PRE,         // z = s * F_x^-1(in0)/npts -> out0; reduce <r,z>, <r_prev,z>, <z,Phi>, <P_prev,Phi>,
+                       // <r,P_prev> (in1 = Phi, in2 = r, in3 = r_prev, in4 = P_prev); fused beta and direction
   ROW_INV_PLAIN,       // out0 = scale * F_x^-1(in0)
   ROW_INV_LIN,         // out0 = H_lin(in2) from T' (in0), G (in1) (no reductions)
   ROW_FWD_UPD,         // Phi (in0, written back to out1) <- pending step with P (in2); out0 = F_x(Phi)

@@ -9,8 +9,7 @@ enum Phase {
   PH_INIT = 0,      // reset per-level flags (flags & 1: also reset counters)
   PH_OBS,           // E, mu, alpha, masses from the H-chain partials
   PH_RES,           // max |r| and the stopping test
-  PH_BETA,          // Polak-Ribiere+ beta
-  PH_CPROJ,         // Re<D, Phi> and the beta = 0 decision of Algorithm 2 Step 2
+  PH_BETA,          // Polak-Ribiere+ beta, Re<D, Phi> and the beta = 0 decision of Algorithm 2 Step 2
   PH_STEP,          // Algorithm 2 (step model, backtracking, update coefficients)
   PH_CLEAR,         // drop the pending-step flag
   PH_NORM,          // 1/sqrt(mass) per solve into norm_scale
@@ -37,7 +36,7 @@ struct ScalarArgs {
   double inv_npts = 0.0;   // 1 / npts
 };
 
-enum ElemMode { EL_DIR = 0, EL_UPDATE, EL_MASS, EL_SCALE };
+enum ElemMode { EL_UPDATE = 0, EL_MASS, EL_SCALE };
 
 template <class T>
 struct ElemArgs {
@@ -51,9 +50,6 @@ struct ElemArgs {
   int bps;            // blocks per solve (divides npts)
   int nsolve;
   int gate;
-  int fuse;           // EL_DIR: the last block runs the PH_CPROJ step
-  unsigned* cnt;
-  ScalarCtx sc;
   int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
 };
 
@@ -82,6 +78,9 @@ struct HyArgs {
   ScalarCtx sc;
 };
 void launch_hy_upd(const HyArgs& a, cudaStream_t st);
+// blocks per solve of k_hy_upd: whole waves of its resident blocks over nsm SMs, the
+// points split evenly (to one) between the blocks
+int hy_blocks_per_solve(const Geo& g, int nsolve, int nsm);
 
 void launch_scalar(const ScalarArgs& a, cudaStream_t st);
 template <class T> void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st);

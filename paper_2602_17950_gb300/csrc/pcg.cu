@@ -9,6 +9,8 @@
 // coefficients are integrals reduced by the P-chain pass.
 #include <math.h>
 
+#include <algorithm>
+
 #include "gpsoc_internal.cuh"
 #include "kernels.cuh"
 #include "scalar.cuh"
@@ -48,7 +50,6 @@ __global__ void k_scalar(ScalarArgs A) {
     case PH_OBS: sc_obs(X, s, scratch); return;
     case PH_RES: sc_res(X, s, scratch); return;
     case PH_BETA: sc_beta(X, s, scratch); return;
-    case PH_CPROJ: sc_cproj(X, s, scratch); return;
     case PH_STEP: sc_step(X, s, scratch); return;
     case PH_CLEAR: if (threadIdx.x == 0) S.pending = 0; return;
     case PH_KIN: {
@@ -82,7 +83,6 @@ __global__ void k_elem(ElemArgs<T> A) {
   using C = cx_t<T>;
   using W = T;   // working precision of the pointwise math; block sums in FP64
   __shared__ double scratch[16 * 8 + 16];
-  __shared__ int last_flag;
   const int bps = A.bps;
   const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
   if (s >= A.nsolve) return;
@@ -92,45 +92,6 @@ __global__ void k_elem(ElemArgs<T> A) {
   const long long npts = A.npts;
   const long long per = npts / bps;
   const long long sbase = (long long)s * 3 * npts + (long long)rb * per;
-  if (MODE == EL_DIR) {
-    // D = -z + beta P_prev (Section 3.1) is not stored: reduce Re<D, Phi>, Re<H Phi, D>,
-    // Re<z, Phi>, Re<H Phi, z> for the projection and the sign test of Algorithm 2 Step 2
-    const W beta = pick<W>(S.beta, S.fbeta);
-    const bool use_prev = pick<W>(S.beta, S.fbeta) != (W)0;
-    W acc[4] = {(W)0, (W)0, (W)0, (W)0};
-    for (long long e = threadIdx.x; e < per; e += blockDim.x) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const long long i = sbase + c * npts + e;
-        const C z = A.in0[i];
-        W dr = -z.x, di = -z.y;
-        if (use_prev) { const C p = A.in1[i]; dr += beta * p.x; di += beta * p.y; }
-        const C f = A.in2[i];
-        const C h = A.in3[i];
-        acc[0] += dr * f.x + di * f.y;
-        acc[1] += h.x * dr + h.y * di;
-        acc[2] += z.x * f.x + z.y * f.y;
-        acc[3] += h.x * z.x + h.y * z.y;
-      }
-    }
-    double v[4];
-    if constexpr (sizeof(W) == 4) {
-      block_reduce_df<4>(acc, v, scratch);
-    } else {
-      for (int k = 0; k < 4; ++k) v[k] = (double)acc[k];
-      const bool mx[4] = {};
-      block_reduce<4>(v, scratch, mx);
-    }
-    if (threadIdx.x == 0) {
-      double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
-      P[(long long)SL_DPHI * A.pmax] = v[0];
-      P[(long long)SL_HD * A.pmax] = v[1];
-      P[(long long)SL_ZPHI * A.pmax] = v[2];
-      P[(long long)SL_HZ * A.pmax] = v[3];
-    }
-    if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_cproj(A.sc, s, scratch);
-    return;
-  }
   W acc = (W)0;
   if (MODE == EL_UPDATE) {
     // Phi <- (cos t Phi + sin t P/||P||) / norm (Eqs. formula-pcg, update); reduce max |dPhi|^2
@@ -180,7 +141,9 @@ __global__ void k_elem(ElemArgs<T> A) {
 // normalisation (<H_lin Phi, Phi>, rho^2, |F|^2, masses) are FP64; the alpha_l pieces
 // V |phi_l|^2 and rho |phi_l|^2, which only shift the preconditioner, are summed from
 // FP32 products in double-float.
-__global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
+constexpr int kHyThreads = 256, kHyBlocksPerSM = 2;
+
+__global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A) {
   __shared__ double scratch[16 * 8 + 16];
   __shared__ int last_flag;
   const int bps = A.bps;
@@ -188,8 +151,9 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
   if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   const SolveState& S = A.st[s];
   const long long npts = A.npts;
-  const long long per = npts / bps;
-  const long long sbase = (long long)s * 3 * npts, ebase = (long long)rb * per;
+  // block rb of the solve takes points [rb npts / bps, (rb + 1) npts / bps)
+  const long long ebase = (long long)rb * npts / bps, per = (long long)(rb + 1) * npts / bps - ebase;
+  const long long sbase = (long long)s * 3 * npts;
   const bool upd = (A.flags & HY_UPD) && S.pending;
   const bool rec = upd && (A.flags & HY_REC);
   const bool red = (A.flags & HY_REDUCE) != 0;
@@ -232,12 +196,15 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
     // H(Phi) = H_lin Phi + c0 rho Phi + c1 (F.f) Phi (Eqs. eigen1-eigen3) and the sums of the
     // energy (Eq. energy) and of alpha_l (Eq. PreCnstAlpha)
     double m[3], rho = 0.0, q = 0.0;
+    float mf[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       m[c] = f[c].x * f[c].x + f[c].y * f[c].y;
       rho += m[c];
       q += f[c].x * hl[c].x + f[c].y * hl[c].y;
-      A.phi32[sbase + c * npts + off] = make_float2((float)f[c].x, (float)f[c].y);
+      const float2 f32 = make_float2((float)f[c].x, (float)f[c].y);
+      A.phi32[sbase + c * npts + off] = f32;
+      mf[c] = f32.x * f32.x + f32.y * f32.y;   // the alpha pieces from the FP32 copy (no FP64 conversions)
     }
     const double ar = f[1].x * f[0].x + f[1].y * f[0].y + f[2].x * f[1].x + f[2].y * f[1].y;
     const double ai = f[1].x * f[0].y - f[1].y * f[0].x + f[2].x * f[1].y - f[2].y * f[1].x;
@@ -262,12 +229,11 @@ __global__ void __launch_bounds__(256) k_hy_upd(HyArgs A) {
     acc[5] += m[2];
     const long long row = off / nx;
     const float V = trap_value<float>(A.trap, A.g, (int)(off - row * nx), (int)(row % ny), (int)(row / ny), off);
-    const float rf = (float)rho;
+    const float rf = mf[0] + mf[1] + mf[2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float mf = (float)m[c];
-      acc32[c] += V * mf;
-      acc32[3 + c] += rf * mf;
+      acc32[c] += V * mf[c];
+      acc32[3 + c] += rf * mf[c];
     }
   }
   double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
@@ -416,13 +382,23 @@ __global__ void k_comp_scale(double2* data, long long npts, const double* mass, 
 // ------------------------------------------------------------------ launchers
 void launch_scalar(const ScalarArgs& a, cudaStream_t st) { k_scalar<<<a.nsolve, kScalarThreads, 0, st>>>(a); }
 
-void launch_hy_upd(const HyArgs& a, cudaStream_t st) { k_hy_upd<<<a.bps * a.nsolve, 256, 0, st>>>(a); }
+void launch_hy_upd(const HyArgs& a, cudaStream_t st) { k_hy_upd<<<a.bps * a.nsolve, kHyThreads, 0, st>>>(a); }
+
+// The pass is FP64-bound: its time is that of the busiest SM.  Two 256-thread blocks
+// are resident per SM, so the grid is a whole number of waves of 2 nsm blocks (split
+// over the solves, rounded up), with about four points per thread at most.
+int hy_blocks_per_solve(const Geo& g, int nsolve, int nsm) {
+  const long long wave = (long long)kHyBlocksPerSM * std::max(nsm, 1);
+  const long long work = (long long)std::max(nsolve, 1) * g.npts;
+  const long long waves = std::max(1LL, (work + wave * kHyThreads * 4 - 1) / (wave * kHyThreads * 4));
+  const long long b = (wave * waves + nsolve - 1) / std::max(nsolve, 1);
+  return (int)std::max(1LL, std::min(b, g.npts));
+}
 
 template <class T>
 void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   const int nb = a.bps * a.nsolve;
   switch (mode) {
-    case EL_DIR: k_elem<T, EL_DIR><<<nb, 256, 0, st>>>(a); break;
     case EL_UPDATE: k_elem<T, EL_UPDATE><<<nb, 256, 0, st>>>(a); break;
     case EL_MASS: k_elem<T, EL_MASS><<<nb, 256, 0, st>>>(a); break;
     case EL_SCALE: k_elem<T, EL_SCALE><<<nb, 256, 0, st>>>(a); break;

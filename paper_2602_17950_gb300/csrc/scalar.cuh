@@ -145,48 +145,36 @@ __device__ __forceinline__ void sc_res(const ScalarCtx& X, int s, double* scratc
   }
 }
 
-// Polak-Ribiere+ beta = max(Re<r - r_prev, P r> / Re<r_prev, P_prev r_prev>, 0)
+// Polak-Ribiere+ beta = max(Re<r - r_prev, P r> / Re<r_prev, P_prev r_prev>, 0), the
+// tangent projection coefficient c = Re<D, Phi> of D = -P r + beta P_prev (Eq. formula-
+// project) and Algorithm 2 Step 2, all from the sums of the preconditioner's last pass:
+// D is linear in beta, so Re<D, Phi> = -Re<z, Phi> + beta Re<P_prev, Phi> and the slope
+// Re<r, D> = -Re<r, z> + beta Re<r, P_prev> (b_n has its sign: Re<H Phi, P> = Re<r, D>
+// for the tangent P).  If the slope is not negative the step restarts from D = -P r.
 __device__ __forceinline__ void sc_beta(const ScalarCtx& X, int s, double* scratch) {
   SolveState& S = X.st[s];
-  double w[2];
-  const int wslots[2] = {SL_RZ, SL_RPZ};
-  slot_totals<2>(X, s, wslots, X.nb_row, w, scratch);
+  double w[5];
+  const int wslots[5] = {SL_RZ, SL_RPZ, SL_ZPHI, SL_PPHI, SL_RP};
+  slot_totals<5>(X, s, wslots, X.nb_row, w, scratch);
   if (threadIdx.x != 0) return;
   const double dV = X.dV;
-  S.s_cur = dV * w[0];
+  const double rz = dV * w[0], zphi = dV * w[2];
+  S.s_cur = rz;
   double beta = 0.0;
   if (!S.first) {
-    beta = (dV * w[0] - dV * w[1]) / S.s_prev;
+    beta = (rz - dV * w[1]) / S.s_prev;
     if (!(beta > 0.0)) beta = 0.0;   // max(beta, 0), NaN -> 0
   }
-  S.beta = beta;
-  S.fbeta = (float)beta;
-}
-
-// Tangent projection coefficient c = Re<D, Phi> (Eq. formula-project), and
-// Algorithm 2 Step 2 decided before the direction is transformed:
-// b_n has the sign of Re<H Phi, P> = Re<H Phi, D> - c mu, so when it is >= 0
-// for D = -P r + beta P_prev the step restarts from D = -P r (beta = 0).
-__device__ __forceinline__ void sc_cproj(const ScalarCtx& X, int s, double* scratch) {
-  SolveState& S = X.st[s];
-  double w[4];
-  const int wslots[4] = {SL_DPHI, SL_HD, SL_ZPHI, SL_HZ};
-  slot_totals<4>(X, s, wslots, X.nb_row, w, scratch);
-  if (threadIdx.x != 0) return;
-  const double dV = X.dV;
-  const double cD = dV * w[0], hD = dV * w[1];
-  // slope of the projected direction: Re<H Phi, D> - c mu, or in GPSOC_HYBRID (whose
-  // pass sums Re<r, D> with the FP64-accurate residual r) Re<r, D> itself
-  const double slope = (X.flags & 8) ? hD : hD - cD * S.mu;
-  if (S.beta != 0.0 && !(slope < 0.0)) {
-    S.beta = 0.0;
+  double cD = -zphi + beta * dV * w[3];
+  if (beta != 0.0 && !(-rz + beta * dV * w[4] < 0.0)) {
+    beta = 0.0;
     S.beta_resets++;
-    S.cproj = -dV * w[2];   // D = -z: Re<D, Phi> = -Re<z, Phi>
-  } else {
-    S.cproj = cD;
+    cD = -zphi;
   }
-  S.fbeta = (float)S.beta;
-  S.fcproj = (float)S.cproj;
+  S.beta = beta;
+  S.cproj = cD;
+  S.fbeta = (float)beta;
+  S.fcproj = (float)cD;
 }
 
 // |P| and the reciprocals of |P| and |P|^2: one square root and one division

@@ -360,7 +360,7 @@ def test_fp32_iteration_kernels_run_at_every_tile_shape(n):
             p.set_initial(psi)
             E0 = p.observables()[0][0]
             prof = p.profile(iters=6, precision=prec)
-            assert len(prof) == 10 and all(ms > 0 for _, ms in prof)
+            assert len(prof) == 9 and all(ms > 0 for _, ms in prof)
             E1, _, m = p.observables()
             assert np.isfinite(E1[0]) and E1[0] < E0
             assert abs(m[0].sum() - 1.0) < 1e-6

@@ -207,4 +207,7 @@ def test_algorithm2_branches_follow_oracle():
     assert res["halvings"] == ref.halvings
     assert res["beta_resets"] == ref.beta_resets
     assert rel_max(got, ref.Phi) < 1e-9
-    assert res["energy"] == pytest.approx(ref.energies[-2], rel=1e-12)
+    # E of an iterate away from the minimum moves to first order with the iterate (bar 1e-9);
+    # with c0 = 2000 the rounding of ten stiff steps reaches about 2e-12 of E, while a
+    # different branch would change E by a whole step's energy change
+    assert res["energy"] == pytest.approx(ref.energies[-2], rel=1e-11)
