@@ -115,10 +115,7 @@ __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&sl
     for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
     block_reduce<K>(v, red, mx);
   }
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) part[(sbase_slot + slots[k]) * pmax + blk] = v[k];
-  }
+  put_partials<K>(part, sbase_slot, pmax, blk, slots, v, mx);
 }
 
 // ============================================================== row passes (x axis)
@@ -136,15 +133,16 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
   const int bps = rows / R;
   const int s = blockIdx.x / bps;
   const int rb = blockIdx.x % bps;
-  if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   C* s_tw = (C*)smem_raw;
+  load_tw<T>(s_tw, A.tw[0], nx, ept);   // constant table: before the wait on the previous kernel
+  pdl_wait();
+  if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   C* buf0 = s_tw + fft_padded_len<C>(nx);
   const int per = R * nx;             // elements of one component in the tile
   const int NP = fft_padded_len<C>(nx), CP = R * NP;   // padded line length, component stride in smem
   constexpr bool two = (MODE == ROW_INV_H || MODE == ROW_INV_P || MODE == ROW_INV_LIN || MODE == ROW_INV_P_HY);
   C* buf1 = buf0 + 3 * CP;
   double* red = (double*)(buf1 + (two ? 3 * CP : 0));
-  load_tw<T>(s_tw, A.tw[0], nx, ept);
   const long long sbase = (long long)s * 3 * npts;
   const long long rbase = (long long)rb * R * nx;   // offset of the tile inside a component
   const long long sslot = (long long)s * NSLOT;
@@ -482,10 +480,9 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
       double v2[2] = {rphi, pp64};
       const bool mx2[2] = {false, false};
       block_reduce<2>(v2, red, mx2);
-      if (threadIdx.x == 0) {
-        A.part[(sslot + SL_RPHI) * A.pmax + rb] = v2[0];
-        A.part[(sslot + SL_P2) * A.pmax + rb] = v2[1];
-      }
+      const int slots2[2] = {SL_RPHI, SL_P2};
+      __syncthreads();   // thread 0 of store_partials wrote SL_RPHI's FP32 sum before
+      put_partials<2>(A.part, sslot, A.pmax, rb, slots2, v2, mx2);
     }
     if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_step(A.sc, s, red);
   }
@@ -529,17 +526,18 @@ __global__ void __launch_bounds__(kThreads) k_col(ChainArgs<T> A, int axis, int 
   const int bps = tpo * no;
   const int s = blockIdx.x / bps;
   const int tb = blockIdx.x % bps;
+  C* s_tw = (C*)smem_raw;
+  load_tw<T>(s_tw, A.tw[axis], na, ept);   // constant table: before the wait on the previous kernel
+  pdl_wait();
   if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
   const int o = tb / tpo;
   const int i0 = (tb % tpo) * TC;
-  C* s_tw = (C*)smem_raw;
   C* buf = s_tw + fft_padded_len<C>(na);
   const int per = na * TC;
   const int NPL = col_line_len<C>(na, TC);        // padded line length
   const int CS = TC * NPL;                     // component stride in smem
   C* buf2 = buf + 3 * CS;            // second 3-component tile (YMID_H, YINV_H)
   double* red = (double*)(buf2 + 3 * CS);
-  load_tw<T>(s_tw, A.tw[axis], na, ept);
   const long long sbase = (long long)s * 3 * npts;
   const long long obase = (long long)o * na * ni + i0;
   const SolveState& S = A.st[s];
@@ -953,10 +951,11 @@ static void row_go(const ChainArgs<T>& a, cudaStream_t st) {
   const int nb = row_blocks_per_solve<T>(a.g, a.nsolve) * a.nsolve;
   const size_t sm = row_smem<T>(a.g, MODE, a.nsolve);
   const int ept = row_ept<T>(a.g, a.nsolve);
+  const int threads = round_threads(3 * R * a.g.n[0] / ept);
   if constexpr (row_lean<T, MODE>())
-    k_row_lean<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
+    launch_pdl(k_row_lean<T, MODE>, nb, threads, sm, st, a, R, ept);
   else
-    k_row<T, MODE><<<nb, round_threads(3 * R * a.g.n[0] / ept), sm, st>>>(a, R, ept);
+    launch_pdl(k_row<T, MODE>, nb, threads, sm, st, a, R, ept);
 }
 
 template <class T>
@@ -982,7 +981,7 @@ static void col_go(int axis, const ChainArgs<T>& a, cudaStream_t st) {
   col_cfg<T>(a.g, axis, a.nsolve, tc, ept, threads);
   const int nb = col_blocks_per_solve<T>(a.g, axis, a.nsolve) * a.nsolve;
   const size_t sm = col_smem<T>(a.g, axis, a.nsolve);
-  k_col<T, MODE><<<nb, threads, sm, st>>>(a, axis, tc, ept);
+  launch_pdl(k_col<T, MODE>, nb, threads, sm, st, a, axis, tc, ept);
 }
 
 template <class T>

@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/gpsoc.h"
 
@@ -57,12 +58,15 @@ struct TrapDev {
 struct PhysDev {
   double Omega, gamma, c0, c1;
   float fOmega, fgamma, fc0, fc1;    // FP32 copies
+  float c0lo, c1lo;                  // c0 - fc0, c1 - fc1: the double-word interaction constants
 };
 
 __host__ __device__ inline PhysDev make_phys(double Omega, double gamma, double c0, double c1) {
   PhysDev p;
   p.Omega = Omega; p.gamma = gamma; p.c0 = c0; p.c1 = c1;
   p.fOmega = (float)Omega; p.fgamma = (float)gamma; p.fc0 = (float)c0; p.fc1 = (float)c1;
+  p.c0lo = (float)(c0 - (double)p.fc0);
+  p.c1lo = (float)(c1 - (double)p.fc1);
   return p;
 }
 
@@ -102,6 +106,8 @@ struct SolveState {
   double acorr;     // radial part Re<P, Phi>/||Phi||^2 removed from the last direction (tangent correction)
   // FP32 copies of the scalars the array passes read (refreshed by mirror32)
   float fmu, fbeta, fcproj, fupd_c, fupd_s, fupd_scale, falpha[3], fpad;
+  // GPSOC_HYBRID: the accepted step as double words (hi, lo): uc = g c, ut = g t and uc - 1
+  float dw_uc[2], dw_ut[2], dw_ucm1[2];
 };
 
 __device__ __forceinline__ void mirror32(SolveState& S) {
@@ -191,6 +197,46 @@ struct ChainArgs {
   int khat_upd;
 };
 
+// Programmatic dependent launch.  The iteration's kernels are launched with programmatic
+// stream serialisation (launch_pdl).  pdl_wait() waits until the kernel before it in the
+// stream has completed and its writes are visible (griddepcontrol.wait); every read of
+// data another kernel writes comes after it, only constant tables are read before.
+// pdl_trigger() (griddepcontrol.launch_dependents) lets the next kernel's blocks be
+// scheduled once every block has issued it or exited.  The passes with a fused scalar
+// tail issue it when a block has written its partial sums (last_block), so the next
+// kernel's blocks are placed on SMs this pass has left, and wait there while the last
+// block runs the tail; the others trigger at exit.  Without the launch attribute (the
+// default) the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// launch with programmatic stream serialisation when GPSOC_PDL=1 is set in the environment
+// (kernels that call pdl_wait before reading what earlier kernels wrote); by default the
+// kernels run in plain stream order, which measured faster for this iteration's kernels
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("GPSOC_PDL");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 __device__ __forceinline__ bool gate_ok(const SolveState* st, int gate, int s) {
   if (gate == GATE_ALL) return true;
   if (gate == GATE_ACTIVE) return st[s].active != 0;
@@ -202,6 +248,7 @@ __device__ __forceinline__ bool gate_ok(const SolveState* st, int gate, int s) {
 // solve s (threadfence-reduction pattern: partial sums written before the
 // arrival are visible to the last block).  The last block resets the counter.
 __device__ __forceinline__ bool last_block(unsigned* cnt, int s, int bps, int* flag_smem) {
+  pdl_trigger();
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -341,6 +388,63 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int ofs) {
   return r;
 }
 
+// Double-word arithmetic for pointwise work that needs more than FP32 but runs where
+// FP64 issue slots are the bound (one FP64 warp instruction per 64 cycles per SM
+// sub-partition on this part).  Operations follow Joldes, Muller and Popescu, "Tight
+// and rigorous error bounds for basic building blocks of double-word arithmetic"
+// (ACM TOMS 2017): the accurate double-word sum (TwoSum of the high and of the low
+// parts, two FastTwoSum renormalisations; relative error below 3u^2, u = 2^-24) and
+// the FMA-based double-word products (DW x DW without the lo x lo term, DW x FP32),
+// relative error a few u^2.  Every step is an explicit round-to-nearest intrinsic,
+// so multiply-add contraction cannot break the error-free transformations.
+__device__ __forceinline__ DF dw_fast_two_sum(float a, float b) {   // needs exponent(a) >= exponent(b)
+  const float s = __fadd_rn(a, b);
+  DF r;
+  r.hi = s;
+  r.lo = __fsub_rn(b, __fsub_rn(s, a));
+  return r;
+}
+__device__ __forceinline__ DF dw_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  DF r;
+  r.hi = s;
+  r.lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return r;
+}
+__device__ __forceinline__ DF dw_add(DF a, DF b) {
+  const DF sh = dw_two_sum(a.hi, b.hi);
+  const DF sl = dw_two_sum(a.lo, b.lo);
+  const DF v = dw_fast_two_sum(sh.hi, __fadd_rn(sh.lo, sl.hi));
+  return dw_fast_two_sum(v.hi, __fadd_rn(sl.lo, v.lo));
+}
+__device__ __forceinline__ DF dw_neg(DF a) { DF r; r.hi = -a.hi; r.lo = -a.lo; return r; }
+__device__ __forceinline__ DF dw_sub(DF a, DF b) { return dw_add(a, dw_neg(b)); }
+__device__ __forceinline__ DF dw_mul(DF a, DF b) {
+  const float ch = __fmul_rn(a.hi, b.hi);
+  const float cl = __fmaf_rn(a.hi, b.hi, -ch);                       // TwoProd: a.hi b.hi = ch + cl
+  const float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
+  return dw_fast_two_sum(ch, __fadd_rn(cl, t));
+}
+__device__ __forceinline__ DF dw_mulf(DF a, float b) {
+  const float ch = __fmul_rn(a.hi, b);
+  const float cl = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -ch));
+  return dw_fast_two_sum(ch, cl);
+}
+// FP64 -> double word (hi the FP32 rounding of x; x - hi is exact in FP64) and back
+__device__ __forceinline__ DF dw_of(double x) {
+  DF r;
+  r.hi = __double2float_rn(x);
+  r.lo = __double2float_rn(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double dw_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+// hi and lo of an FP64 value, for state fields the double-word kernels read
+__host__ __device__ inline void dw_split(double x, float* hl) {
+  hl[0] = (float)x;
+  hl[1] = (float)(x - (double)hl[0]);
+}
+
 // One FP32 block total (a sum in double-float, or a max in FP32, which is exact),
 // rounded to FP64 once.  scratch: >= blockDim.x / 32 + 1 doubles.
 __device__ __forceinline__ double block_reduce1_f(float a, bool is_max, double* scratch) {
@@ -368,19 +472,23 @@ __device__ __forceinline__ double block_reduce1_f(float a, bool is_max, double* 
   return scratch[nw];
 }
 
-// Block sums of FP32 per-thread partials in double-float, same fixed order and
-// same reduce-scatter scheme as block_reduce; the K totals are rounded to FP64
-// once at the end.  scratch: >= 16 * (blockDim.x / 32) + 16 doubles.
+// Block sums of double-float per-thread partials, same fixed order and same
+// reduce-scatter scheme as block_reduce, with the accurate double-word sum; the K
+// totals are rounded to FP64 once at the end.  scratch: >= 16 * (blockDim.x / 32) + 16
+// doubles.
 template <int K>
-__device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)[K], double* scratch) {
-  static_assert(K >= 2 && K <= 16, "block_reduce_df handles 2..16 values");
+__device__ __forceinline__ void block_reduce_dw(const DF (&a)[K], double (&v)[K], double* scratch) {
+  static_assert(K >= 2 && K <= 16, "block_reduce_dw handles 2..16 values");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   __syncthreads();  // scratch may alias shared memory the caller used just before
   constexpr int KP = (K <= 2) ? 2 : (K <= 4) ? 4 : (K <= 8) ? 8 : 16;
   constexpr int LB = (KP == 2) ? 1 : (KP == 4) ? 2 : (KP == 8) ? 3 : 4;
   DF x[KP];
 #pragma unroll
-  for (int k = 0; k < KP; ++k) { x[k].hi = (k < K) ? a[k] : 0.0f; x[k].lo = 0.0f; }
+  for (int k = 0; k < KP; ++k) {
+    x[k].hi = (k < K) ? a[k].hi : 0.0f;
+    x[k].lo = (k < K) ? a[k].lo : 0.0f;
+  }
 #pragma unroll
   for (int st = 0; st < LB; ++st) {
     const int ofs = 1 << st, half = (KP / 2) >> st;
@@ -389,11 +497,11 @@ __device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)
     for (int i = 0; i < half; ++i) {
       const DF keep = up ? x[i + half] : x[i];
       const DF send = up ? x[i] : x[i + half];
-      x[i] = df_add(keep, df_shfl_xor(send, ofs));
+      x[i] = dw_add(keep, df_shfl_xor(send, ofs));
     }
   }
 #pragma unroll
-  for (int ofs = KP; ofs < 32; ofs <<= 1) x[0] = df_add(x[0], df_shfl_xor(x[0], ofs));
+  for (int ofs = KP; ofs < 32; ofs <<= 1) x[0] = dw_add(x[0], df_shfl_xor(x[0], ofs));
   int slot = 0;
 #pragma unroll
   for (int b = 0; b < LB; ++b) slot |= ((lane >> b) & 1) << (LB - 1 - b);
@@ -406,13 +514,60 @@ __device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)
     DF acc{f.x, f.y};
     for (int w = 1; w < nw; ++w) {
       const float2 g = sc2[w * 16 + threadIdx.x];
-      acc = df_add(acc, DF{g.x, g.y});
+      acc = dw_add(acc, DF{g.x, g.y});
     }
     res[threadIdx.x] = (double)acc.hi + (double)acc.lo;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = res[k];
+}
+// the same for FP32 per-thread partials
+template <int K>
+__device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)[K], double* scratch) {
+  DF x[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { x[k].hi = a[k]; x[k].lo = 0.0f; }
+  block_reduce_dw<K>(x, v, scratch);
+}
+
+// Per-block partials in the part buffer: a sum is stored as a double word (FP32 hi, lo
+// packed into the 8-byte slot), a maximum as FP64.  The scalar tail that adds a solve's
+// partials then works on the FP32 pipes (it runs on one SM, where every FP64 warp
+// instruction costs 64 cycles of a sub-partition).
+__device__ __forceinline__ void put_partial(double* p, double v, bool is_max) {
+  if (is_max) {
+    *p = v;
+    return;
+  }
+  const float hi = __double2float_rn(v);
+  *reinterpret_cast<float2*>(p) = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__device__ __forceinline__ DF get_sum_partial(const double* p) {
+  const float2 w = __ldcg(reinterpret_cast<const float2*>(p));
+  DF r;
+  r.hi = w.x;
+  r.lo = w.y;
+  return r;
+}
+// threads k < K of the block store slot k of the block totals v (v and slots identical
+// in every thread); the value is picked by selects so that the K conversions are one
+// instruction of the first warp
+template <int K>
+__device__ __forceinline__ void put_partials(double* part, long long sbase_slot, int pmax, int blk,
+                                             const int (&slots)[K], const double (&v)[K], const bool (&mx)[K]) {
+  const int t = threadIdx.x;
+  if (t >= K) return;
+  double vk = v[0];
+  int sk = slots[0];
+  bool mk_ = mx[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) {
+    vk = (t == k) ? v[k] : vk;
+    sk = (t == k) ? slots[k] : sk;
+    mk_ = (t == k) ? mx[k] : mk_;
+  }
+  put_partial(part + (sbase_slot + sk) * pmax + blk, vk, mk_);
 }
 
 // ------------------------------------------------------------------ host-side launch helpers

@@ -21,6 +21,7 @@ static constexpr int kScalarThreads = 128;
 
 __global__ void k_scalar(ScalarArgs A) {
   __shared__ double scratch[16 * 8 + 16];
+  pdl_wait();
   const int s = blockIdx.x;
   if (s >= A.nsolve) return;
   SolveState& S = A.st[s];
@@ -83,6 +84,7 @@ __global__ void k_elem(ElemArgs<T> A) {
   using C = cx_t<T>;
   using W = T;   // working precision of the pointwise math; block sums in FP64
   __shared__ double scratch[16 * 8 + 16];
+  pdl_wait();
   const int bps = A.bps;
   const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
   if (s >= A.nsolve) return;
@@ -132,20 +134,24 @@ __global__ void k_elem(ElemArgs<T> A) {
   block_reduce<1>(v, scratch, mx);
   if (threadIdx.x == 0) {
     const int slot = (MODE == EL_UPDATE) ? SL_DPHIINF : SL_NORM;
-    A.part[((long long)s * NSLOT + slot) * A.pmax + rb] = v[0];
+    put_partial(A.part + ((long long)s * NSLOT + slot) * A.pmax + rb, v[0], MODE == EL_UPDATE);
   }
 }
 
-// GPSOC_HYBRID opening pass (see HyArgs).  Same block decomposition as the row
-// passes.  The state, H_lin Phi, H(Phi) and the sums that set the energy, mu and the
-// normalisation (<H_lin Phi, Phi>, rho^2, |F|^2, masses) are FP64; the alpha_l pieces
-// V |phi_l|^2 and rho |phi_l|^2, which only shift the preconditioner, are summed from
-// FP32 products in double-float.
+// GPSOC_HYBRID opening pass (see HyArgs).  The state, H_lin Phi and H(Phi) are stored in
+// FP64, and every value the energy, mu, the residual and the normalisation depend on carries
+// about 48 significant bits: the pointwise arithmetic runs in double words (FP32 pairs) on
+// the FP32 pipes, because this part issues one FP64 warp instruction per 64 cycles per SM
+// sub-partition; FP64 instructions remain only to split the loaded values and to round
+// the stored ones.  The alpha_l pieces V |phi_l|^2 and rho |phi_l|^2, which only shift
+// the preconditioner, are FP32 products; max |Phi' - Phi|^2 is taken from the high words.
+// The block sums are double-word; the grid sums of the fused tail are FP64.
 constexpr int kHyThreads = 256, kHyBlocksPerSM = 2;
 
 __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A) {
   __shared__ double scratch[16 * 8 + 16];
   __shared__ int last_flag;
+  pdl_wait();
   const int bps = A.bps;
   const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
   if (s >= A.nsolve || !gate_ok(A.st, A.gate, s)) return;
@@ -157,76 +163,95 @@ __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A)
   const bool upd = (A.flags & HY_UPD) && S.pending;
   const bool rec = upd && (A.flags & HY_REC);
   const bool red = (A.flags & HY_REDUCE) != 0;
-  // Phi' = g (c Phi + t P): with uc = g c, ut = g t, and the change Phi' - Phi = (uc - 1) Phi + ut P
-  const double uc = S.upd_scale * S.upd_c, ut = S.upd_scale * S.upd_s, ucm1 = uc - 1.0;
+  // Phi' = g (c Phi + t P) = uc Phi + ut P, as the change (uc - 1) Phi + ut P added to Phi
+  // (uc = g c, ut = g t split into double words by the step that accepted them)
+  const DF uc = DF{S.dw_uc[0], S.dw_uc[1]}, ut = DF{S.dw_ut[0], S.dw_ut[1]};
+  const DF ucm1 = DF{S.dw_ucm1[0], S.dw_ucm1[1]};
   const PhysDev ph = A.phys[s];
-  const double c0 = ph.c0, c1 = ph.c1;
+  const DF c0 = DF{ph.fc0, ph.c0lo}, c1 = DF{ph.fc1, ph.c1lo};
   const int nx = A.g.n[0], ny = A.g.n[1];
-  double acc[6];
+  DF acc[6];
   float acc32[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) { acc[k] = 0.0; acc32[k] = 0.0f; }
-  double dmax = 0.0;
+  for (int k = 0; k < 6; ++k) { acc[k] = DF{0.0f, 0.0f}; acc32[k] = 0.0f; }
+  float dmax = 0.0f;
   for (long long e = threadIdx.x; e < per; e += blockDim.x) {
     const long long off = ebase + e;
-    double2 f[3], hl[3];
+    // every load of the point first (one memory round trip), then the arithmetic
+    double2 f64[3], h64[3];
+    float2 q[3], hq[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long i = sbase + c * npts + off;
-      f[c] = A.phi[i];
-      if (red && !rec) hl[c] = A.hl[i];
+      f64[c] = A.phi[i];
+      if (red || rec) h64[c] = A.hl[i];
+      if (upd) q[c] = A.p[i];
+      if (rec) hq[c] = A.hlp[i];
+    }
+    DF fx[3], fy[3], hx[3], hy[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long i = sbase + c * npts + off;
+      fx[c] = dw_of(f64[c].x);
+      fy[c] = dw_of(f64[c].y);
+      if (red && !rec) {
+        hx[c] = dw_of(h64[c].x);
+        hy[c] = dw_of(h64[c].y);
+      }
       if (upd) {
         // the accepted step (Eqs. formula-pcg, update) with the exact tangent direction
-        const float2 q = A.p[i];
-        const double qx = (double)q.x, qy = (double)q.y;
-        const double dr = ucm1 * f[c].x + ut * qx, di = ucm1 * f[c].y + ut * qy;
-        dmax = fmax(dmax, dr * dr + di * di);
-        f[c] = make_double2(f[c].x + dr, f[c].y + di);
-        A.phi[i] = f[c];
+        const DF dx = dw_add(dw_mul(ucm1, fx[c]), dw_mulf(ut, q[c].x));
+        const DF dy = dw_add(dw_mul(ucm1, fy[c]), dw_mulf(ut, q[c].y));
+        dmax = fmaxf(dmax, dx.hi * dx.hi + dy.hi * dy.hi);
+        fx[c] = dw_add(fx[c], dx);
+        fy[c] = dw_add(fy[c], dy);
+        A.phi[i] = make_double2(dw_to_double(fx[c]), dw_to_double(fy[c]));
         if (rec) {
           // H_lin is linear: H_lin Phi' = g (c H_lin Phi + t H_lin P)
-          const double2 h0 = A.hl[i];
-          const float2 hq = A.hlp[i];
-          hl[c] = make_double2(uc * h0.x + ut * (double)hq.x, uc * h0.y + ut * (double)hq.y);
-          A.hl[i] = hl[c];
+          hx[c] = dw_add(dw_mul(uc, dw_of(h64[c].x)), dw_mulf(ut, hq[c].x));
+          hy[c] = dw_add(dw_mul(uc, dw_of(h64[c].y)), dw_mulf(ut, hq[c].y));
+          A.hl[i] = make_double2(dw_to_double(hx[c]), dw_to_double(hy[c]));
         }
       }
     }
     if (!red) continue;
     // H(Phi) = H_lin Phi + c0 rho Phi + c1 (F.f) Phi (Eqs. eigen1-eigen3) and the sums of the
     // energy (Eq. energy) and of alpha_l (Eq. PreCnstAlpha)
-    double m[3], rho = 0.0, q = 0.0;
+    DF m[3];
     float mf[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      m[c] = f[c].x * f[c].x + f[c].y * f[c].y;
-      rho += m[c];
-      q += f[c].x * hl[c].x + f[c].y * hl[c].y;
-      const float2 f32 = make_float2((float)f[c].x, (float)f[c].y);
-      A.phi32[sbase + c * npts + off] = f32;
-      mf[c] = f32.x * f32.x + f32.y * f32.y;   // the alpha pieces from the FP32 copy (no FP64 conversions)
+      m[c] = dw_add(dw_mul(fx[c], fx[c]), dw_mul(fy[c], fy[c]));
+      acc[0] = dw_add(acc[0], dw_add(dw_mul(fx[c], hx[c]), dw_mul(fy[c], hy[c])));
+      A.phi32[sbase + c * npts + off] = make_float2(fx[c].hi, fy[c].hi);
+      mf[c] = fx[c].hi * fx[c].hi + fy[c].hi * fy[c].hi;   // the alpha pieces (FP32)
     }
-    const double ar = f[1].x * f[0].x + f[1].y * f[0].y + f[2].x * f[1].x + f[2].y * f[1].y;
-    const double ai = f[1].x * f[0].y - f[1].y * f[0].x + f[2].x * f[1].y - f[2].y * f[1].x;
-    const double Fz = m[0] - m[2];
-    double fr[3], fi[3];
-    fr[0] = Fz * f[0].x + (ar * f[1].x - ai * f[1].y);
-    fi[0] = Fz * f[0].y + (ar * f[1].y + ai * f[1].x);
-    fr[1] = (ar * f[0].x + ai * f[0].y) + (ar * f[2].x - ai * f[2].y);
-    fi[1] = (ar * f[0].y - ai * f[0].x) + (ar * f[2].y + ai * f[2].x);
-    fr[2] = (ar * f[1].x + ai * f[1].y) - Fz * f[2].x;
-    fi[2] = (ar * f[1].y - ai * f[1].x) - Fz * f[2].y;
-    const double c0r = c0 * rho;
+    const DF rho = dw_add(dw_add(m[0], m[1]), m[2]);
+    // a = phi_1 conj(phi_0) + phi_0 conj(phi_-1) (components ordered 1, 0, -1), Fz = |phi_1|^2 - |phi_-1|^2
+    const DF ar = dw_add(dw_add(dw_mul(fx[1], fx[0]), dw_mul(fy[1], fy[0])),
+                         dw_add(dw_mul(fx[2], fx[1]), dw_mul(fy[2], fy[1])));
+    const DF ai = dw_add(dw_sub(dw_mul(fx[1], fy[0]), dw_mul(fy[1], fx[0])),
+                         dw_sub(dw_mul(fx[2], fy[1]), dw_mul(fy[2], fx[1])));
+    const DF Fz = dw_sub(m[0], m[2]);
+    DF fr[3], fi[3];
+    fr[0] = dw_add(dw_mul(Fz, fx[0]), dw_sub(dw_mul(ar, fx[1]), dw_mul(ai, fy[1])));
+    fi[0] = dw_add(dw_mul(Fz, fy[0]), dw_add(dw_mul(ar, fy[1]), dw_mul(ai, fx[1])));
+    fr[1] = dw_add(dw_add(dw_mul(ar, fx[0]), dw_mul(ai, fy[0])), dw_sub(dw_mul(ar, fx[2]), dw_mul(ai, fy[2])));
+    fi[1] = dw_add(dw_sub(dw_mul(ar, fy[0]), dw_mul(ai, fx[0])), dw_add(dw_mul(ar, fy[2]), dw_mul(ai, fx[2])));
+    fr[2] = dw_sub(dw_add(dw_mul(ar, fx[1]), dw_mul(ai, fy[1])), dw_mul(Fz, fx[2]));
+    fi[2] = dw_sub(dw_sub(dw_mul(ar, fy[1]), dw_mul(ai, fx[1])), dw_mul(Fz, fy[2]));
+    const DF c0r = dw_mul(c0, rho);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      A.hphi[sbase + c * npts + off] =
-          make_double2(hl[c].x + c0r * f[c].x + c1 * fr[c], hl[c].y + c0r * f[c].y + c1 * fi[c]);
-    acc[0] += q;
-    acc[1] += rho * rho;
-    acc[2] += 2.0 * (ar * ar + ai * ai) + Fz * Fz;
-    acc[3] += m[0];
-    acc[4] += m[1];
-    acc[5] += m[2];
+    for (int c = 0; c < 3; ++c) {
+      const DF hr = dw_add(dw_add(hx[c], dw_mul(c0r, fx[c])), dw_mul(c1, fr[c]));
+      const DF hi = dw_add(dw_add(hy[c], dw_mul(c0r, fy[c])), dw_mul(c1, fi[c]));
+      A.hphi[sbase + c * npts + off] = make_double2(dw_to_double(hr), dw_to_double(hi));
+    }
+    acc[1] = dw_add(acc[1], dw_mul(rho, rho));
+    const DF a2 = dw_add(dw_mul(ar, ar), dw_mul(ai, ai));
+    acc[2] = dw_add(acc[2], dw_add(dw_add(a2, a2), dw_mul(Fz, Fz)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[3 + c] = dw_add(acc[3 + c], m[c]);
     const long long row = off / nx;
     const float V = trap_value<float>(A.trap, A.g, (int)(off - row * nx), (int)(row % ny), (int)(row / ny), off);
     const float rf = mf[0] + mf[1] + mf[2];
@@ -238,25 +263,18 @@ __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A)
   }
   double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
   if (upd) {
-    double v1[1] = {dmax};
-    const bool mx1[1] = {true};
-    block_reduce<1>(v1, scratch, mx1);
-    if (threadIdx.x == 0) P[(long long)SL_DPHIINF * A.pmax] = v1[0];
+    const double v = block_reduce1_f(dmax, true, scratch);
+    if (threadIdx.x == 0) put_partial(P + (long long)SL_DPHIINF * A.pmax, v, true);
   }
   if (!red) return;
-  const bool mx[6] = {};
-  block_reduce<6>(acc, scratch, mx);
-  double v32[6];
-  block_reduce_df<6>(acc32, v32, scratch);
-  if (threadIdx.x == 0) {
-    const int slots[6] = {SL_Q, SL_RHO2, SL_F2, SL_M0, SL_M1, SL_M2};
-    const int slots32[6] = {SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2};
+  DF all[12];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      P[(long long)slots[k] * A.pmax] = acc[k];
-      P[(long long)slots32[k] * A.pmax] = v32[k];
-    }
-  }
+  for (int k = 0; k < 6; ++k) { all[k] = acc[k]; all[6 + k] = DF{acc32[k], 0.0f}; }
+  double v[12];
+  block_reduce_dw<12>(all, v, scratch);
+  const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_M0, SL_M1, SL_M2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2};
+  const bool mx[12] = {};
+  put_partials<12>(A.part, (long long)s * NSLOT, A.pmax, rb, slots, v, mx);
   if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, scratch);
 }
 
@@ -380,9 +398,13 @@ __global__ void k_comp_scale(double2* data, long long npts, const double* mass, 
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_scalar(const ScalarArgs& a, cudaStream_t st) { k_scalar<<<a.nsolve, kScalarThreads, 0, st>>>(a); }
+void launch_scalar(const ScalarArgs& a, cudaStream_t st) {
+  launch_pdl(k_scalar, a.nsolve, kScalarThreads, 0, st, a);
+}
 
-void launch_hy_upd(const HyArgs& a, cudaStream_t st) { k_hy_upd<<<a.bps * a.nsolve, kHyThreads, 0, st>>>(a); }
+void launch_hy_upd(const HyArgs& a, cudaStream_t st) {
+  launch_pdl(k_hy_upd, a.bps * a.nsolve, kHyThreads, 0, st, a);
+}
 
 // The pass is FP64-bound: its time is that of the busiest SM.  Two 256-thread blocks
 // are resident per SM, so the grid is a whole number of waves of 2 nsm blocks (split
@@ -399,9 +421,9 @@ template <class T>
 void launch_elem(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   const int nb = a.bps * a.nsolve;
   switch (mode) {
-    case EL_UPDATE: k_elem<T, EL_UPDATE><<<nb, 256, 0, st>>>(a); break;
-    case EL_MASS: k_elem<T, EL_MASS><<<nb, 256, 0, st>>>(a); break;
-    case EL_SCALE: k_elem<T, EL_SCALE><<<nb, 256, 0, st>>>(a); break;
+    case EL_UPDATE: launch_pdl(k_elem<T, EL_UPDATE>, nb, 256, 0, st, a); break;
+    case EL_MASS: launch_pdl(k_elem<T, EL_MASS>, nb, 256, 0, st, a); break;
+    case EL_SCALE: launch_pdl(k_elem<T, EL_SCALE>, nb, 256, 0, st, a); break;
   }
 }
 

@@ -10,23 +10,31 @@
 namespace gpsoc {
 
 // K slot totals (sums over the nb block partials of solve s); every thread gets them.
-// The K partials of a block index are loaded together (one memory round trip per
-// blockDim partials, not one per slot).
+// The partials are double words (put_partial): a thread adds its share with the accurate
+// double-word sum and the block adds the threads' shares the same way, all on the FP32
+// pipes; the K totals are rounded to FP64 once.  The K partials of a block index are
+// loaded together (one memory round trip per blockDim partials, not one per slot).
 template <int K>
 __device__ __forceinline__ void slot_totals(const ScalarCtx& X, int s, const int (&slots)[K], int nb, double (&v)[K],
                                             double* scratch) {
-  const bool mx[K] = {};
+  constexpr int K2 = (K < 2) ? 2 : K;
   const double* base = X.part + (long long)s * NSLOT * X.pmax;
+  DF w[K2];
+  int b = threadIdx.x;
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    double t[K];
+  for (int k = 0; k < K2; ++k)
+    w[k] = (k < K && b < nb) ? get_sum_partial(base + (long long)slots[k < K ? k : 0] * X.pmax + b) : DF{0.0f, 0.0f};
+  for (b += blockDim.x; b < nb; b += blockDim.x) {
+    DF t[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = __ldcg(base + (long long)slots[k] * X.pmax + b);
+    for (int k = 0; k < K; ++k) t[k] = get_sum_partial(base + (long long)slots[k] * X.pmax + b);
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += t[k];
+    for (int k = 0; k < K; ++k) w[k] = dw_add(w[k], t[k]);
   }
-  block_reduce<K>(v, scratch, mx);
+  double r[K2];
+  block_reduce_dw<K2>(w, r, scratch);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = r[k];
 }
 
 __device__ __forceinline__ double slot_max(const ScalarCtx& X, int s, int slot, int nb, double* scratch) {
@@ -365,6 +373,13 @@ __device__ __forceinline__ void step_decide(const ScalarCtx& X, int s, SolveStat
   // Phi' = (cos t Phi + sin t P_t/|P_t|)/norm with P_t = P - a Phi tangent: |.|^2 = c^2 M + s'^2 |P_t|^2
   const double nrm2 = cs * cs * M + sp * sp * S.P2;
   S.upd_c = cs - sp * S.acorr; S.upd_s = sp; S.upd_scale = rsqrt(nrm2);
+  if (X.flags & 8) {
+    // GPSOC_HYBRID: the double-word coefficients the opening pass applies
+    const double uc = S.upd_scale * S.upd_c;
+    dw_split(uc, S.dw_uc);
+    dw_split(S.upd_scale * S.upd_s, S.dw_ut);
+    dw_split(uc - 1.0, S.dw_ucm1);
+  }
   S.pending = 1;
   S.last_par = (X.flags >> 2) & 1;
   S.iters++; S.total_iters++;
