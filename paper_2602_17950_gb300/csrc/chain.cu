@@ -115,7 +115,7 @@ __device__ __forceinline__ void store_partials(const W (&acc)[K], const int (&sl
     for (int k = 0; k < K; ++k) v[k] = (double)acc[k];
     block_reduce<K>(v, red, mx);
   }
-  put_partials<K>(part, sbase_slot, pmax, blk, slots, v, mx);
+  put_partials<K>(part, sbase_slot, pmax, blk, slots, v, mx, sizeof(W) == 4);
 }
 
 // ============================================================== row passes (x axis)
@@ -482,7 +482,7 @@ __device__ __forceinline__ void row_pass(const ChainArgs<T>& A, int R, int ept) 
       block_reduce<2>(v2, red, mx2);
       const int slots2[2] = {SL_RPHI, SL_P2};
       __syncthreads();   // thread 0 of store_partials wrote SL_RPHI's FP32 sum before
-      put_partials<2>(A.part, sslot, A.pmax, rb, slots2, v2, mx2);
+      put_partials<2>(A.part, sslot, A.pmax, rb, slots2, v2, mx2, true);
     }
     if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_step(A.sc, s, red);
   }

@@ -289,6 +289,7 @@ ScalarArgs scalar_args(gpsoc_problem* p, int level, int phase, const Geo& g) {
   s.phase = phase;
   s.npts = g.npts;
   s.inv_npts = 1.0 / (double)g.npts;
+  s.part_dw = sizeof(T) == 4 ? 1 : 0;
   s.dV = g.dV;
   s.norm_scale = p->d_scale;
   (void)level;
@@ -309,6 +310,7 @@ ScalarCtx scalar_ctx(gpsoc_problem* p, const Geo& g, const OptsDev& o, int flags
   c.opts = o;
   c.flags = flags;
   c.inv_npts = 1.0 / (double)g.npts;
+  c.part_dw = sizeof(T) == 4 ? 1 : 0;
   return c;
 }
 

@@ -167,6 +167,7 @@ struct ScalarCtx {
                         // 8 = GPSOC_HYBRID iteration (kinetic part of alpha from the state, residual-based
                         //     slopes: the H Phi slots hold Re<r, .> sums)
   double inv_npts;      // 1 / npts
+  int part_dw;          // the sum partials it reads are double words (written by FP32 / hybrid passes)
 };
 
 template <class T>
@@ -431,14 +432,52 @@ __device__ __forceinline__ DF dw_mulf(DF a, float b) {
   const float cl = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -ch));
   return dw_fast_two_sum(ch, cl);
 }
-// FP64 -> double word (hi the FP32 rounding of x; x - hi is exact in FP64) and back
+// FP64 <-> double word without FP64 conversions: on this part F2F conversions occupy the
+// FP64 pipe like an FP64 add, so the fields of the IEEE 754 encodings are moved with
+// integer operations instead.
+// binary32 -> binary64, exact for normal values, zero, inf and NaN (FP32 subnormals, below
+// 2^-126, become signed zeros)
+__device__ __forceinline__ double widen_f(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = u & 0x7f800000u, sign = u & 0x80000000u;
+  // exponent field rebiased by 1023 - 127 = 896, mantissa moved to the top of 52 bits
+  unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+  unsigned lo = u << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 0x7f800000u) hi |= 0x7ff00000u;   // inf and NaN stay non-finite
+  return __hiloint2double((int)hi, (int)lo);
+}
+// binary64 -> double word: hi = x rounded to 24 significant bits (half-ulp ties up),
+// lo = x - hi rounded to FP32, so |lo| <= ulp(hi)/2 and hi + lo = x to 2^-48 relative
+// (a double word holds 48 of the 53 bits).  The 29 low bits of x become FP32 values by
+// exact subtractions 1.m 2^q - 2^q, which normalise them.  Finite x with |x| < 2^-126
+// gives 0 (its low word vanishes below 2^-80); x beyond the FP32 range gives inf, NaN
+// stays NaN.
 __device__ __forceinline__ DF dw_of(double x) {
+  const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
+  const unsigned sign = H & 0x80000000u;
+  const int E = (int)((H >> 20) & 0x7ffu);                   // biased binary64 exponent
+  const unsigned up = (L >> 28) & 1u;                          // first dropped bit: round up
   DF r;
-  r.hi = __double2float_rn(x);
-  r.lo = __double2float_rn(x - (double)r.hi);
+  // the carry of the rounding runs into the exponent field by itself
+  r.hi = __uint_as_float((sign | ((unsigned)(E - 896) << 23) | ((H & 0xfffffu) << 3) | (L >> 29)) + up);
+  // bits 28..6 of L, weight 2^(E-1069) each: (1 + m 2^-23) 2^(E-1046) - 2^(E-1046), less one
+  // more 2^(E-1046) (the unit added to hi) when rounded up
+  const unsigned t1 = sign | ((unsigned)(E - 919) << 23);
+  const float a = __fsub_rn(__uint_as_float(t1 | ((L >> 6) & 0x7fffffu)), __uint_as_float(t1 + (up << 23)));
+  // bits 5..0 of L, weight 2^(E-1075): (1 + m 2^-6) 2^(E-1069) - 2^(E-1069)
+  const unsigned t2 = sign | ((unsigned)(E - 942) << 23);
+  const float b = __fsub_rn(__uint_as_float(t2 | ((L & 0x3fu) << 17)), __uint_as_float(t2));
+  r.lo = (E >= 943) ? __fadd_rn(a, b) : ((E >= 920) ? a : 0.0f);
+  if (E < 897) r.hi = __uint_as_float(sign);
+  if (E > 1150) {
+    r.hi = (E == 2047 && ((H & 0xfffffu) | L) != 0u) ? __int_as_float(0x7fc00000) : __uint_as_float(sign | 0x7f800000u);
+    r.lo = 0.0f;
+  }
   return r;
 }
-__device__ __forceinline__ double dw_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+// double word -> binary64, correctly rounded: one FP64 add of the two exact widenings
+__device__ __forceinline__ double dw_to_double(DF a) { return widen_f(a.hi) + widen_f(a.lo); }
 // hi and lo of an FP64 value, for state fields the double-word kernels read
 __host__ __device__ inline void dw_split(double x, float* hl) {
   hl[0] = (float)x;
@@ -531,12 +570,13 @@ __device__ __forceinline__ void block_reduce_df(const float (&a)[K], double (&v)
   block_reduce_dw<K>(x, v, scratch);
 }
 
-// Per-block partials in the part buffer: a sum is stored as a double word (FP32 hi, lo
-// packed into the 8-byte slot), a maximum as FP64.  The scalar tail that adds a solve's
-// partials then works on the FP32 pipes (it runs on one SM, where every FP64 warp
-// instruction costs 64 cycles of a sub-partition).
-__device__ __forceinline__ void put_partial(double* p, double v, bool is_max) {
-  if (is_max) {
+// Per-block partials in the part buffer.  The FP32 and hybrid passes store a sum as a
+// double word (FP32 hi, lo packed into the 8-byte slot), so that the scalar tail adding
+// a solve's partials works on the FP32 pipes (it runs on one SM, where every FP64 warp
+// instruction costs 64 cycles of a sub-partition); the FP64 passes store FP64 sums, and
+// every pass stores maxima as FP64.  The reading tail knows the format (part_dw).
+__device__ __forceinline__ void put_partial(double* p, double v, bool is_max, bool dw) {
+  if (is_max || !dw) {
     *p = v;
     return;
   }
@@ -555,7 +595,8 @@ __device__ __forceinline__ DF get_sum_partial(const double* p) {
 // instruction of the first warp
 template <int K>
 __device__ __forceinline__ void put_partials(double* part, long long sbase_slot, int pmax, int blk,
-                                             const int (&slots)[K], const double (&v)[K], const bool (&mx)[K]) {
+                                             const int (&slots)[K], const double (&v)[K], const bool (&mx)[K],
+                                             bool dw) {
   const int t = threadIdx.x;
   if (t >= K) return;
   double vk = v[0];
@@ -567,7 +608,7 @@ __device__ __forceinline__ void put_partials(double* part, long long sbase_slot,
     sk = (t == k) ? slots[k] : sk;
     mk_ = (t == k) ? mx[k] : mk_;
   }
-  put_partial(part + (sbase_slot + sk) * pmax + blk, vk, mk_);
+  put_partial(part + (sbase_slot + sk) * pmax + blk, vk, mk_, dw);
 }
 
 // ------------------------------------------------------------------ host-side launch helpers

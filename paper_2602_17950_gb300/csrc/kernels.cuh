@@ -34,6 +34,7 @@ struct ScalarArgs {
   const double* thetas; int n_theta; double* model_out;
   int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
   double inv_npts = 0.0;   // 1 / npts
+  int part_dw = 0;    // the sum partials it reads are double words (FP32 passes wrote them)
 };
 
 enum ElemMode { EL_UPDATE = 0, EL_MASS, EL_SCALE };

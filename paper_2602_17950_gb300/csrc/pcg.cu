@@ -28,7 +28,7 @@ __global__ void k_scalar(ScalarArgs A) {
   const int ph_ = A.phase;
   if (A.only >= 0 && s != A.only) return;
   if (ph_ != PH_INIT && ph_ != PH_NORM && !A.force && !S.active) return;
-  ScalarCtx X{A.st, A.phys, A.part, A.pmax, A.nb_row, A.nb_col, A.npts, A.dV, A.opts, A.flags, A.inv_npts};
+  ScalarCtx X{A.st, A.phys, A.part, A.pmax, A.nb_row, A.nb_col, A.npts, A.dV, A.opts, A.flags, A.inv_npts, A.part_dw};
   switch (ph_) {
     case PH_INIT:
       if (threadIdx.x == 0) {
@@ -134,7 +134,7 @@ __global__ void k_elem(ElemArgs<T> A) {
   block_reduce<1>(v, scratch, mx);
   if (threadIdx.x == 0) {
     const int slot = (MODE == EL_UPDATE) ? SL_DPHIINF : SL_NORM;
-    put_partial(A.part + ((long long)s * NSLOT + slot) * A.pmax + rb, v[0], MODE == EL_UPDATE);
+    put_partial(A.part + ((long long)s * NSLOT + slot) * A.pmax + rb, v[0], MODE == EL_UPDATE, sizeof(T) == 4);
   }
 }
 
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A)
   double* P = A.part + (long long)s * NSLOT * A.pmax + rb;
   if (upd) {
     const double v = block_reduce1_f(dmax, true, scratch);
-    if (threadIdx.x == 0) put_partial(P + (long long)SL_DPHIINF * A.pmax, v, true);
+    if (threadIdx.x == 0) put_partial(P + (long long)SL_DPHIINF * A.pmax, v, true, true);
   }
   if (!red) return;
   DF all[12];
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A)
   block_reduce_dw<12>(all, v, scratch);
   const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_M0, SL_M1, SL_M2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2};
   const bool mx[12] = {};
-  put_partials<12>(A.part, (long long)s * NSLOT, A.pmax, rb, slots, v, mx);
+  put_partials<12>(A.part, (long long)s * NSLOT, A.pmax, rb, slots, v, mx, true);
   if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, scratch);
 }
 

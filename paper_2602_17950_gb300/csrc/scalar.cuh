@@ -10,31 +10,45 @@
 namespace gpsoc {
 
 // K slot totals (sums over the nb block partials of solve s); every thread gets them.
-// The partials are double words (put_partial): a thread adds its share with the accurate
-// double-word sum and the block adds the threads' shares the same way, all on the FP32
-// pipes; the K totals are rounded to FP64 once.  The K partials of a block index are
-// loaded together (one memory round trip per blockDim partials, not one per slot).
+// The K partials of a block index are loaded together (one memory round trip per
+// blockDim partials, not one per slot), and the first partial of a thread is taken as it
+// is.  Double-word partials (X.part_dw) are added with the accurate double-word sum on
+// the FP32 pipes and the totals rounded to FP64 once; FP64 partials are added in FP64.
 template <int K>
 __device__ __forceinline__ void slot_totals(const ScalarCtx& X, int s, const int (&slots)[K], int nb, double (&v)[K],
                                             double* scratch) {
-  constexpr int K2 = (K < 2) ? 2 : K;
   const double* base = X.part + (long long)s * NSLOT * X.pmax;
-  DF w[K2];
   int b = threadIdx.x;
+  if (X.part_dw) {
+    constexpr int K2 = (K < 2) ? 2 : K;
+    DF w[K2];
 #pragma unroll
-  for (int k = 0; k < K2; ++k)
-    w[k] = (k < K && b < nb) ? get_sum_partial(base + (long long)slots[k < K ? k : 0] * X.pmax + b) : DF{0.0f, 0.0f};
-  for (b += blockDim.x; b < nb; b += blockDim.x) {
-    DF t[K];
+    for (int k = 0; k < K2; ++k)
+      w[k] = (k < K && b < nb) ? get_sum_partial(base + (long long)slots[k < K ? k : 0] * X.pmax + b) : DF{0.0f, 0.0f};
+    for (b += blockDim.x; b < nb; b += blockDim.x) {
+      DF t[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = get_sum_partial(base + (long long)slots[k] * X.pmax + b);
+      for (int k = 0; k < K; ++k) t[k] = get_sum_partial(base + (long long)slots[k] * X.pmax + b);
 #pragma unroll
-    for (int k = 0; k < K; ++k) w[k] = dw_add(w[k], t[k]);
+      for (int k = 0; k < K; ++k) w[k] = dw_add(w[k], t[k]);
+    }
+    double r[K2];
+    block_reduce_dw<K2>(w, r, scratch);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = r[k];
+    return;
   }
-  double r[K2];
-  block_reduce_dw<K2>(w, r, scratch);
+  const bool mx[K] = {};
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = r[k];
+  for (int k = 0; k < K; ++k) v[k] = (b < nb) ? __ldcg(base + (long long)slots[k] * X.pmax + b) : 0.0;
+  for (b += blockDim.x; b < nb; b += blockDim.x) {
+    double t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = __ldcg(base + (long long)slots[k] * X.pmax + b);
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += t[k];
+  }
+  block_reduce<K>(v, scratch, mx);
 }
 
 __device__ __forceinline__ double slot_max(const ScalarCtx& X, int s, int slot, int nb, double* scratch) {
