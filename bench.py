@@ -144,7 +144,9 @@ HYBRID_BYTES = {"hy_upd": 104, "row_fwd_pre_hy": 48, "coly_mid_pre": 16, "row_in
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu
 # on the kernel inside this workload: (kernel, grid points per axis, 1 = FP32 / 0 = FP64).
 # At 128^2 the arrays stay in L2 (0 bytes written back during the launch).
-NCU_DRAM_BYTES = {("coly_ymid_h", 128, 0): 869888.0}
+NCU_DRAM_BYTES = {("coly_ymid_h", 128, 0): 869888.0,
+                  # ncu --set full, one launch of the 256^2 kernel case (inputs L2-resident: reads only)
+                  ("row_inv_p_hy", 256, 2): 11141632.0}
 
 
 def launch_bytes(name: str, n, prec: int) -> float:
