@@ -577,7 +577,7 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
   h.fuse = (flags & HY_REDUCE) ? 1 : 0;
   h.cnt = p->d_cnt;
   h.sc = sc;
-  h.sc.nb_row = h.bps;                // its fused tail sums the partials this pass wrote
+  h.sc.nb_row = h.bps;                // the observables step sums the partials this pass wrote
   return h;
 }
 

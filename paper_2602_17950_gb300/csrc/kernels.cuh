@@ -54,11 +54,12 @@ struct ElemArgs {
   int only = -1;      // >= 0: act on this solve only (per-slot operations of the server)
 };
 
-// GPSOC_HYBRID: the FP64 pass that opens an iteration.  HY_UPD applies the pending
-// step Phi <- s (c Phi + t P) (P in FP32), HY_REC advances H_lin Phi by the same
-// linear combination of H_lin Phi and H_lin P, HY_REDUCE forms the nonlinear terms,
-// the energy / mu / alpha / mass sums of the FP64 state, writes the FP32 copy of Phi
-// and runs the observables step in the last block of each solve.
+// GPSOC_HYBRID: the pass that opens an iteration (FP64 state, double-word arithmetic).
+// HY_UPD applies the pending step Phi <- s (c Phi + t P) (P in FP32), HY_REC advances
+// H_lin Phi by the same linear combination of H_lin Phi and H_lin P, HY_REDUCE forms the
+// nonlinear terms and H(Phi), the per-block energy / mu / alpha / mass sums and the FP32
+// copy of Phi.  With fuse set, the observables step runs in the last block of each solve;
+// the iteration launches it as its own kernel instead (HY in gpsoc.cu).
 enum { HY_UPD = 1, HY_REC = 2, HY_REDUCE = 4 };
 struct HyArgs {
   SolveState* st;

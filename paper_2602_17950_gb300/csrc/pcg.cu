@@ -145,7 +145,8 @@ __global__ void k_elem(ElemArgs<T> A) {
 // sub-partition; FP64 instructions remain only to split the loaded values and to round
 // the stored ones.  The alpha_l pieces V |phi_l|^2 and rho |phi_l|^2, which only shift
 // the preconditioner, are FP32 products; max |Phi' - Phi|^2 is taken from the high words.
-// The block sums are double-word; the grid sums of the fused tail are FP64.
+// The block sums are double words, stored as double-word partials for the observables
+// step (grid sums on the FP32 pipes, totals rounded to FP64).
 constexpr int kHyThreads = 256, kHyBlocksPerSM = 2;
 
 __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A) {
