@@ -15,6 +15,7 @@
 #include <stdlib.h>
 
 #include "../../include/gpsoc.h"
+#include "dword.cuh"
 
 namespace gpsoc {
 
@@ -370,7 +371,6 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* scratch, co
 // value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  Sums use
 // Knuth's TwoSum (an error-free transformation), so adding FP32 per-thread
 // partials this way is as accurate as FP64 adds while issuing on the FP32 pipes.
-struct DF { float hi, lo; };
 __device__ __forceinline__ DF df_add(DF a, DF b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
@@ -387,101 +387,6 @@ __device__ __forceinline__ DF df_shfl_xor(DF a, int ofs) {
   r.hi = __shfl_xor_sync(0xffffffffu, a.hi, ofs);
   r.lo = __shfl_xor_sync(0xffffffffu, a.lo, ofs);
   return r;
-}
-
-// Double-word arithmetic for pointwise work that needs more than FP32 but runs where
-// FP64 issue slots are the bound (one FP64 warp instruction per 64 cycles per SM
-// sub-partition on this part).  Operations follow Joldes, Muller and Popescu, "Tight
-// and rigorous error bounds for basic building blocks of double-word arithmetic"
-// (ACM TOMS 2017): the accurate double-word sum (TwoSum of the high and of the low
-// parts, two FastTwoSum renormalisations; relative error below 3u^2, u = 2^-24) and
-// the FMA-based double-word products (DW x DW without the lo x lo term, DW x FP32),
-// relative error a few u^2.  Every step is an explicit round-to-nearest intrinsic,
-// so multiply-add contraction cannot break the error-free transformations.
-__device__ __forceinline__ DF dw_fast_two_sum(float a, float b) {   // needs exponent(a) >= exponent(b)
-  const float s = __fadd_rn(a, b);
-  DF r;
-  r.hi = s;
-  r.lo = __fsub_rn(b, __fsub_rn(s, a));
-  return r;
-}
-__device__ __forceinline__ DF dw_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  DF r;
-  r.hi = s;
-  r.lo = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return r;
-}
-__device__ __forceinline__ DF dw_add(DF a, DF b) {
-  const DF sh = dw_two_sum(a.hi, b.hi);
-  const DF sl = dw_two_sum(a.lo, b.lo);
-  const DF v = dw_fast_two_sum(sh.hi, __fadd_rn(sh.lo, sl.hi));
-  return dw_fast_two_sum(v.hi, __fadd_rn(sl.lo, v.lo));
-}
-__device__ __forceinline__ DF dw_neg(DF a) { DF r; r.hi = -a.hi; r.lo = -a.lo; return r; }
-__device__ __forceinline__ DF dw_sub(DF a, DF b) { return dw_add(a, dw_neg(b)); }
-__device__ __forceinline__ DF dw_mul(DF a, DF b) {
-  const float ch = __fmul_rn(a.hi, b.hi);
-  const float cl = __fmaf_rn(a.hi, b.hi, -ch);                       // TwoProd: a.hi b.hi = ch + cl
-  const float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
-  return dw_fast_two_sum(ch, __fadd_rn(cl, t));
-}
-__device__ __forceinline__ DF dw_mulf(DF a, float b) {
-  const float ch = __fmul_rn(a.hi, b);
-  const float cl = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -ch));
-  return dw_fast_two_sum(ch, cl);
-}
-// FP64 <-> double word without FP64 conversions: on this part F2F conversions occupy the
-// FP64 pipe like an FP64 add, so the fields of the IEEE 754 encodings are moved with
-// integer operations instead.
-// binary32 -> binary64, exact for normal values, zero, inf and NaN (FP32 subnormals, below
-// 2^-126, become signed zeros)
-__device__ __forceinline__ double widen_f(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = u & 0x7f800000u, sign = u & 0x80000000u;
-  // exponent field rebiased by 1023 - 127 = 896, mantissa moved to the top of 52 bits
-  unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
-  unsigned lo = u << 29;
-  if (e == 0u) { hi = sign; lo = 0u; }
-  if (e == 0x7f800000u) hi |= 0x7ff00000u;   // inf and NaN stay non-finite
-  return __hiloint2double((int)hi, (int)lo);
-}
-// binary64 -> double word: hi = x rounded to 24 significant bits (half-ulp ties up),
-// lo = x - hi rounded to FP32, so |lo| <= ulp(hi)/2 and hi + lo = x to 2^-48 relative
-// (a double word holds 48 of the 53 bits).  The 29 low bits of x become FP32 values by
-// exact subtractions 1.m 2^q - 2^q, which normalise them.  Finite x with |x| < 2^-126
-// gives 0 (its low word vanishes below 2^-80); x beyond the FP32 range gives inf, NaN
-// stays NaN.
-__device__ __forceinline__ DF dw_of(double x) {
-  const unsigned H = (unsigned)__double2hiint(x), L = (unsigned)__double2loint(x);
-  const unsigned sign = H & 0x80000000u;
-  const int E = (int)((H >> 20) & 0x7ffu);                   // biased binary64 exponent
-  const unsigned up = (L >> 28) & 1u;                          // first dropped bit: round up
-  DF r;
-  // the carry of the rounding runs into the exponent field by itself
-  r.hi = __uint_as_float((sign | ((unsigned)(E - 896) << 23) | ((H & 0xfffffu) << 3) | (L >> 29)) + up);
-  // bits 28..6 of L, weight 2^(E-1069) each: (1 + m 2^-23) 2^(E-1046) - 2^(E-1046), less one
-  // more 2^(E-1046) (the unit added to hi) when rounded up
-  const unsigned t1 = sign | ((unsigned)(E - 919) << 23);
-  const float a = __fsub_rn(__uint_as_float(t1 | ((L >> 6) & 0x7fffffu)), __uint_as_float(t1 + (up << 23)));
-  // bits 5..0 of L, weight 2^(E-1075): (1 + m 2^-6) 2^(E-1069) - 2^(E-1069)
-  const unsigned t2 = sign | ((unsigned)(E - 942) << 23);
-  const float b = __fsub_rn(__uint_as_float(t2 | ((L & 0x3fu) << 17)), __uint_as_float(t2));
-  r.lo = (E >= 943) ? __fadd_rn(a, b) : ((E >= 920) ? a : 0.0f);
-  if (E < 897) r.hi = __uint_as_float(sign);
-  if (E > 1150) {
-    r.hi = (E == 2047 && ((H & 0xfffffu) | L) != 0u) ? __int_as_float(0x7fc00000) : __uint_as_float(sign | 0x7f800000u);
-    r.lo = 0.0f;
-  }
-  return r;
-}
-// double word -> binary64, correctly rounded: one FP64 add of the two exact widenings
-__device__ __forceinline__ double dw_to_double(DF a) { return widen_f(a.hi) + widen_f(a.lo); }
-// hi and lo of an FP64 value, for state fields the double-word kernels read
-__host__ __device__ inline void dw_split(double x, float* hl) {
-  hl[0] = (float)x;
-  hl[1] = (float)(x - (double)hl[0]);
 }
 
 // One FP32 block total (a sum in double-float, or a max in FP32, which is exact),
