@@ -575,7 +575,6 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
   h.gate = gate;
   h.flags = flags;
   h.fuse = (flags & HY_REDUCE) ? 1 : 0;
-  h.cnt = p->d_cnt;
   h.sc = sc;
   h.sc.nb_row = h.bps;                // the observables step sums the partials this pass wrote
   return h;
@@ -587,9 +586,7 @@ HyArgs hy_args(gpsoc_problem* p, int level, const Geo& g, const ScalarCtx& sc, i
 // (ncu, 256^2) against 11k for the same step alone; the iteration measured 1-2% faster
 // with the separate launch.
 void HY(gpsoc_problem* p, const HyArgs& h) {
-  HyArgs k = h;
-  k.fuse = 0;
-  launch_hy_upd(k, p->stream);
+  launch_hy_upd(h, p->stream);
   mark(p, (h.flags & HY_REDUCE) ? "hy_upd" : "hy_step");
   if (h.fuse) {
     ScalarArgs x{};

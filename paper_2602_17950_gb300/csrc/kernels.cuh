@@ -58,8 +58,8 @@ struct ElemArgs {
 // HY_UPD applies the pending step Phi <- s (c Phi + t P) (P in FP32), HY_REC advances
 // H_lin Phi by the same linear combination of H_lin Phi and H_lin P, HY_REDUCE forms the
 // nonlinear terms and H(Phi), the per-block energy / mu / alpha / mass sums and the FP32
-// copy of Phi.  With fuse set, the observables step runs in the last block of each solve;
-// the iteration launches it as its own kernel instead (HY in gpsoc.cu).
+// copy of Phi.  The observables step that consumes the sums runs as its own kernel after
+// it when fuse is set (HY in gpsoc.cu).
 enum { HY_UPD = 1, HY_REC = 2, HY_REDUCE = 4 };
 struct HyArgs {
   SolveState* st;
@@ -75,9 +75,8 @@ struct HyArgs {
   double2* hphi;         // H(Phi) = H_lin Phi + nonlinear terms (FP64), written by HY_REDUCE
   long long npts;
   int bps, nsolve, gate, flags;
-  int fuse;
-  unsigned* cnt;
-  ScalarCtx sc;
+  int fuse;              // HY: run the observables step on the sums afterwards
+  ScalarCtx sc;          // scalar context of that step
 };
 void launch_hy_upd(const HyArgs& a, cudaStream_t st);
 // blocks per solve of k_hy_upd: whole waves of its resident blocks over nsm SMs, the

@@ -151,7 +151,6 @@ constexpr int kHyThreads = 256, kHyBlocksPerSM = 2;
 
 __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A) {
   __shared__ double scratch[16 * 8 + 16];
-  __shared__ int last_flag;
   pdl_wait();
   const int bps = A.bps;
   const int s = blockIdx.x / bps, rb = blockIdx.x % bps;
@@ -276,7 +275,6 @@ __global__ void __launch_bounds__(kHyThreads, kHyBlocksPerSM) k_hy_upd(HyArgs A)
   const int slots[12] = {SL_Q, SL_RHO2, SL_F2, SL_M0, SL_M1, SL_M2, SL_V0, SL_V1, SL_V2, SL_C0, SL_C1, SL_C2};
   const bool mx[12] = {};
   put_partials<12>(A.part, (long long)s * NSLOT, A.pmax, rb, slots, v, mx, true);
-  if (A.fuse && last_block(A.cnt, s, bps, &last_flag)) sc_obs(A.sc, s, scratch);
 }
 
 // zero-pad the full spectrum of level N (in) into level 2N (out, zeroed first)
