@@ -17,8 +17,22 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gpsoc_internal.cuh"
 #include "kernels.cuh"
+
+// NVTX ranges around the host-side phases (a solve, each multigrid level, the FP64
+// lead-in, the hybrid verification, the autotuner, a server step), for timeline tools
+// (ncu --nvtx, Nsight Systems); without an attached tool the calls return at once.
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace gpsoc;
 
@@ -726,6 +740,7 @@ gpsoc_status build_graph_hy(gpsoc_problem* p, int level, const OptsDev& o, bool 
 // whose exact residual misses the rule continues (*resumed counts them).  Buffer
 // parity 0 is used, the parity the next iteration graph starts with.
 gpsoc_status hy_verify(gpsoc_problem* p, int level, const OptsDev& o, int* resumed) {
+  NvtxRange range("gpsoc hybrid verification");
   *resumed = 0;
   const Geo g = make_geo(p, level);
   OptsDev ov = o;
@@ -812,6 +827,14 @@ gpsoc_status iterate_until_done_hy(gpsoc_problem* p, int level, const OptsDev& o
 // then PCG in FP64 from that iterate (beta restarted) to the stopping rule.
 gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_every, bool first_level,
                        int precision, double fp32_rel, bool carry, int refresh, double lead_res) {
+  char rname[96];
+  {
+    const Geo gl = make_geo(p, level);
+    const char* pn = precision == GPSOC_HYBRID ? "hybrid" : (precision == GPSOC_MIXED ? "mixed" : "fp64");
+    if (p->dim == 2) snprintf(rname, sizeof rname, "gpsoc level %dx%d %s", gl.n[0], gl.n[1], pn);
+    else snprintf(rname, sizeof rname, "gpsoc level %dx%dx%d %s", gl.n[0], gl.n[1], gl.n[2], pn);
+  }
+  NvtxRange range(rname);
   gpsoc_status s;
   if (precision == GPSOC_HYBRID) {
     s = ensure_fp32(p);
@@ -822,6 +845,7 @@ gpsoc_status run_level(gpsoc_problem* p, int level, const OptsDev& o, int check_
       // FP64 iterations until max|r| < lead_res on the first level (the early iterations
       // from the initial guess decide which local minimum the solve reaches; finer levels
       // start from the prolonged solution of that minimum)
+      NvtxRange lead("gpsoc fp64 lead-in");
       s = iterate_until_done<double>(p, level, lead_opts(o, lead_res), check_every);
       if (s != GPSOC_OK) return s;
       s = init_level(p, level, false);
@@ -1285,6 +1309,7 @@ gpsoc_status gpsoc_set_initial_kind(gpsoc_problem* p, const int kind[3], int lev
 }
 
 gpsoc_status gpsoc_solve(gpsoc_problem* p, const gpsoc_opts* opts, gpsoc_result* results) {
+  NvtxRange range("gpsoc_solve");
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!opts) return fail(GPSOC_EINVAL, "opts is NULL");
@@ -1583,6 +1608,7 @@ gpsoc_status gpsoc_tuning_set(const gpsoc_problem* p, int level, int axis, int p
 }
 
 gpsoc_status gpsoc_autotune(gpsoc_problem* p, const gpsoc_opts* opts, int iters, int* lines, int* elems_per_thread) {
+  NvtxRange range("gpsoc_autotune");
   g_err.clear();
   if (check_problem(p) != GPSOC_OK) return GPSOC_EINVAL;
   if (!opts) return fail(GPSOC_EINVAL, "opts is NULL");
@@ -1940,6 +1966,7 @@ using Clock = std::chrono::steady_clock;
 // until `deadline`, after which it goes on to admission and launches without
 // retiring anything.
 gpsoc_status server_step_impl(gpsoc_server* s, int* busy, bool bounded, Clock::time_point deadline) {
+  NvtxRange range("gpsoc server step");
   gpsoc_status err = GPSOC_OK;
   // 1. buckets whose round of iterations finished: retire the solves that stopped.
   //    If no bucket has finished yet, wait for the one launched first.
