@@ -17,7 +17,12 @@
 #include <thread>
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define GPSOC_HAVE_NVTX 1
+#else
+#define GPSOC_HAVE_NVTX 0
+#endif
 
 #include "gpsoc_internal.cuh"
 #include "kernels.cuh"
@@ -27,8 +32,12 @@
 // (ncu --nvtx, Nsight Systems); without an attached tool the calls return at once.
 namespace {
 struct NvtxRange {
+#if GPSOC_HAVE_NVTX
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
   ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char*) {}   // toolkit without the NVTX headers: no ranges
+#endif
   NvtxRange(const NvtxRange&) = delete;
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
